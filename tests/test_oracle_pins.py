@@ -1,0 +1,439 @@
+"""Pins of the FP64 oracle to what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the
+paper's printed stencils (Tables 1 and 2, transcribed under tests/golden/),
+closed forms (Neumann cosine modes, polynomial exactness), exact invariants
+(equilibria of eq. (1), conservation, transpose symmetry, 1D reduction), the
+qualitative regimes of Section 2, and finite differences of the forward map
+for the discrete adjoint.  None needs a GPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_01748_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------- eq. (2)
+
+def test_tensor_is_rotated_diagonal():
+    """A = R(theta) diag(l1, l2) R^T: eigenvalues l1, l2 and the eigenvector of
+    l1 along (cos theta, sin theta)."""
+    th = inputs.white_noise(7, 5, 11, 0.0, math.pi)
+    l1 = inputs.white_noise(7, 5, 12, 0.1, 1.0)
+    l2 = inputs.white_noise(7, 5, 13, 0.01, 0.09)   # l2 < l1 everywhere
+    a11, a12, a22 = oracle.coefficients(th, l1, l2)
+    for k in range(th.size):
+        A = np.array([[a11.flat[k], a12.flat[k]], [a12.flat[k], a22.flat[k]]])
+        w, v = np.linalg.eigh(A)
+        assert np.allclose(w, [l2.flat[k], l1.flat[k]], rtol=0, atol=1e-15)
+        e1 = np.array([math.cos(th.flat[k]), math.sin(th.flat[k])])
+        assert abs(abs(e1 @ v[:, 1]) - 1.0) < 1e-14
+
+
+def test_lambda_max_matches_eigvalsh():
+    a11 = inputs.white_noise(9, 4, 21, 0.1, 1.0)
+    a22 = inputs.white_noise(9, 4, 22, 0.1, 1.0)
+    a12 = inputs.white_noise(9, 4, 23, -0.3, 0.3)
+    ref = max(np.linalg.eigvalsh(np.array([[a, b], [b, c]])).max()
+              for a, b, c in zip(a11.flat, a12.flat, a22.flat))
+    assert abs(oracle.lambda_max(a11, a12, a22) - ref) < 1e-15
+
+
+def test_dt_rule_below_diffusion_bound():
+    """dt_max never exceeds h^2 / (4 Lambda) on a square grid; with
+    c = rho = delta = 0 only the logistic rate 1 of U remains beside it."""
+    h = 1.0 / 128
+    assert oracle.dt_max(h, h, 1.0, 0.0, 0.0, 0.0, 0.0) == pytest.approx(1.0 / (4.0 / (h * h) + 1.0), rel=1e-15)
+    for lam, delta, c in [(1.0, 12.5, 70.0), (0.01, 0.5, 70.0), (0.3, 20.0, 5.0)]:
+        assert oracle.dt_max(h, h, lam, delta, 1.0, 4e-5, c) < h * h / (4.0 * lam)
+    # Lambda is at least D
+    assert oracle.dt_max(h, h, 1e-6, 0, 0, 1e-3, 0) == pytest.approx(1.0 / (4e-3 / (h * h) + 1.0), rel=1e-15)
+
+
+def test_dt_rule_keeps_diagonals_nonnegative():
+    """Under CFL <= 1 every diagonal coefficient of eq. (3) is >= 0 for a12 = 0:
+    the counterexample that rules out min(diffusion, reaction) bounds."""
+    for (h, lam, delta, rho, D, c) in [(1 / 100, 0.003, 0.5, 1, 4e-5, 70), (1 / 128, 1.0, 12.5, 1, 4e-5, 70),
+                                       (1 / 16, 0.01, 20, 1, 1e-3, 70)]:
+        dt = oracle.dt_max(h, h, lam, delta, rho, D, c)
+        assert 1 - dt * (c + 4 * lam / h ** 2) >= 0        # W centre
+        assert 1 - dt * (1 + delta) >= 0                   # U (U, W <= 1)
+        assert 1 - dt * 4 * max(lam, D) / h ** 2 >= 0      # V centre
+
+
+# --------------------------------------------------------------- Tables 1, 2
+
+def _read_stencil(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            ox, oy, expr = line.split(None, 2)
+            rows.append((int(ox), int(oy), expr))
+    assert len(rows) == 9
+    return rows
+
+
+def _dense_from_table(rows, nx, ny, dx, dy, fields):
+    """Dense operator assembled straight from a table, interior rows only."""
+    n = nx * ny
+    M = np.zeros((n, n))
+    for j in range(1, ny - 1):
+        for i in range(1, nx - 1):
+            env = {"dx": dx, "dy": dy}
+            for name, F in fields.items():
+                env[name] = (lambda F: (lambda p, q: F[j + q, i + p]))(F)
+            for ox, oy, expr in rows:
+                M[j * nx + i, (j + oy) * nx + (i + ox)] += eval(expr, {"__builtins__": {}}, env)
+    return M
+
+
+def _interior(nx, ny):
+    return np.array([j * nx + i for j in range(1, ny - 1) for i in range(1, nx - 1)])
+
+
+def test_table1_tumour_stencil_literal():
+    nx, ny = 7, 6
+    dx, dy = 1.0 / nx, 1.3 / ny
+    U = inputs.white_noise(nx, ny, 31)
+    M = _dense_from_table(_read_stencil("table1_tumour_stencil.txt"), nx, ny, dx, dy, {"U": U})
+    rows = _interior(nx, ny)
+    for k in range(nx * ny):
+        e = np.zeros(nx * ny)
+        e[k] = 1.0
+        col = oracle.tumour_operator(U, e.reshape(ny, nx), dx, dy).ravel()
+        scale = 1.0 / min(dx, dy) ** 2
+        assert np.max(np.abs(col[rows] - M[rows, k])) <= 1e-13 * scale
+
+
+def test_table2_acid_stencil_literal():
+    nx, ny = 7, 6
+    dx, dy = 1.0 / nx, 1.3 / ny
+    a = inputs.white_noise(nx, ny, 41, 0.1, 1.0)
+    b = inputs.white_noise(nx, ny, 42, -0.4, 0.4)
+    c = inputs.white_noise(nx, ny, 43, 0.1, 1.0)
+    M = _dense_from_table(_read_stencil("table2_acid_stencil.txt"), nx, ny, dx, dy, {"a": a, "b": b, "c": c})
+    rows = _interior(nx, ny)
+    for k in range(nx * ny):
+        e = np.zeros(nx * ny)
+        e[k] = 1.0
+        col = oracle.acid_operator(a, b, c, e.reshape(ny, nx), dx, dy).ravel()
+        scale = 1.0 / min(dx, dy) ** 2
+        assert np.max(np.abs(col[rows] - M[rows, k])) <= 1e-13 * scale
+
+
+def test_tables_have_zero_row_sums():
+    """Both printed stencils annihilate constants (a property of the tables)."""
+    nx, ny = 5, 5
+    U = inputs.white_noise(nx, ny, 51)
+    a, b, c = (inputs.white_noise(nx, ny, s, 0.1, 1.0) for s in (52, 53, 54))
+    for name, fields in [("table1_tumour_stencil.txt", {"U": U}),
+                         ("table2_acid_stencil.txt", {"a": a, "b": b, "c": c})]:
+        M = _dense_from_table(_read_stencil(name), nx, ny, 0.2, 0.2, fields)
+        assert np.max(np.abs(M[_interior(nx, ny)].sum(axis=1))) < 1e-10
+
+
+# --------------------------------------------------------------- invariants
+
+def _hetero(nx, ny, seed):
+    th, l1, l2 = inputs.heterogeneous_tensor(nx, ny, seed, 0.1, 1.0)
+    return oracle.coefficients(th, l1, l2)
+
+
+@pytest.mark.parametrize("state", [(1.0, 0.0, 0.0), (0.0, 1.0, 1.0), (0.0, 0.0, 0.0), (0.5, 1.0, 1.0)])
+def test_constant_equilibria_bitwise(state):
+    """(1,0,0), (0,1,1), (0,0,0) and (1-delta,1,1) with delta = 1/2 zero every
+    rate of eq. (1) and every stencil difference, for any heterogeneous A."""
+    nx, ny = 13, 9
+    a = _hetero(nx, ny, 61)
+    s = oracle.Setup(nx, ny, 0.5, 1.0, 4e-5, 70.0, 1e-4)
+    U, V, W = (np.full((ny, nx), v) for v in state)
+    U1, V1, W1 = oracle.run(s, *a, U, V, W, 50)
+    assert np.array_equal(U1, U) and np.array_equal(V1, V) and np.array_equal(W1, W)
+
+
+def test_mass_conservation_without_reactions():
+    """Zero boundary flux and the flux form conserve sum V and sum W."""
+    nx, ny = 24, 20
+    p = inputs.plain_128(nx, ny)
+    s, a = oracle.setup_for(p, no_reaction=True)
+    s.D = 1e-2  # make the tumour flux non-trivial
+    U, V, W = inputs.random_state(nx, ny, 71)
+    m0 = oracle.diagnostics(U, V, W, s.dx, s.dy)["mass"]
+    U1, V1, W1 = oracle.run(s, *a, U, V, W, 2000)
+    m1 = oracle.diagnostics(U1, V1, W1, s.dx, s.dy)["mass"]
+    assert np.array_equal(U1, U)
+    assert abs(m1[1] - m0[1]) <= 1e-13 * m0[1]
+    assert abs(m1[2] - m0[2]) <= 1e-13 * m0[2]
+    assert np.max(np.abs(W1 - W)) > 1e-3  # it did move
+
+
+def test_transpose_symmetry_bitwise():
+    """Swapping x and y (a11 <-> a22, nx <-> ny, dx <-> dy, fields transposed)
+    transposes the result exactly."""
+    nx, ny = 11, 7
+    a11, a12, a22 = _hetero(nx, ny, 81)
+    U, V, W = inputs.random_state(nx, ny, 82)
+    s = oracle.Setup(nx, ny, 3.0, 1.0, 3e-3, 70.0, 2e-5, lx=1.0, ly=0.8)
+    sT = oracle.Setup(ny, nx, 3.0, 1.0, 3e-3, 70.0, 2e-5, lx=0.8, ly=1.0)
+    r = oracle.run(s, a11, a12, a22, U, V, W, 30)
+    rT = oracle.run(sT, a22.T, a12.T, a11.T, U.T, V.T, W.T, 30)
+    for f, g in zip(r, rT):
+        assert np.array_equal(f, g.T)
+
+
+@pytest.mark.parametrize("k,l", [(1, 0), (2, 3), (5, 1)])
+def test_neumann_cosine_closed_form(k, l):
+    """Isotropic constant kappa, no reactions: cos(k pi x) cos(l pi y) at cell
+    centres is an eigenvector of the zero-flux operator with eigenvalue
+    -4 kappa [sin^2(k pi dx / 2)/dx^2 + sin^2(l pi dy / 2)/dy^2]."""
+    nx, ny, kappa = 16, 12, 0.7
+    s = oracle.Setup(nx, ny, 0.0, 0.0, 0.0, 0.0, 0.0, no_reaction=True)
+    s.dt = 0.45 / (2 * kappa * (1 / s.dx ** 2 + 1 / s.dy ** 2))
+    x = (np.arange(nx) + 0.5) * s.dx
+    y = (np.arange(ny) + 0.5) * s.dy
+    W0 = np.outer(np.cos(l * math.pi * y), np.cos(k * math.pi * x))
+    g = 1 - 4 * s.dt * kappa * (math.sin(k * math.pi * s.dx / 2) ** 2 / s.dx ** 2
+                                + math.sin(l * math.pi * s.dy / 2) ** 2 / s.dy ** 2)
+    A = np.full((ny, nx), kappa), np.zeros((ny, nx)), np.full((ny, nx), kappa)
+    n = 40
+    _, _, Wn = oracle.run(s, *A, np.zeros((ny, nx)), np.zeros((ny, nx)), W0, n)
+    assert np.max(np.abs(Wn - g ** n * W0)) < 1e-13
+
+
+def test_polynomial_exactness_interior():
+    """On cells away from the boundary: W = x^2, xy, y^2 with constant A gives
+    D2 = 2 a11, 2 a12, 2 a22; W = x^2 with a11 = x gives 4x; V = x^2 with
+    U = x gives D1 = 2 - 4x."""
+    nx, ny = 10, 8
+    dx, dy = 1.0 / nx, 1.0 / ny
+    x = ((np.arange(nx) + 0.5) * dx)[None, :] * np.ones((ny, 1))
+    y = ((np.arange(ny) + 0.5) * dy)[:, None] * np.ones((1, nx))
+    inner = (slice(1, ny - 1), slice(1, nx - 1))
+    A = (np.full((ny, nx), 0.8), np.full((ny, nx), -0.3), np.full((ny, nx), 0.5))
+    for Wf, expect in [(x * x, 2 * 0.8), (x * y, 2 * -0.3), (y * y, 2 * 0.5)]:
+        d2 = oracle.acid_operator(*A, Wf, dx, dy)
+        assert np.max(np.abs(d2[inner] - expect)) < 1e-11
+    d2 = oracle.acid_operator(x, np.zeros_like(x), np.ones_like(x), x * x, dx, dy)
+    assert np.max(np.abs(d2[inner] - 4 * x[inner])) < 1e-11
+    d1 = oracle.tumour_operator(x, x * x, dx, dy)
+    assert np.max(np.abs(d1[inner] - (2 - 4 * x[inner]))) < 1e-11
+
+
+def test_positivity_isotropic_and_parity_of_anisotropic_minimum():
+    """With a12 = 0 the CFL step keeps U in [0,1] and V, W >= 0 (a monotone
+    scheme).  With a12 != 0 the corner coefficients of Table 2 have both signs,
+    so W >= 0 is not guaranteed: only U, V bounds are asserted."""
+    nx = ny = 48
+    p = inputs.plain_128(nx, ny, steps=600)
+    th0 = np.zeros_like(p.theta)
+    s, a = oracle.setup_for(p)
+    a_iso = oracle.coefficients(th0, p.lambda1, p.lambda2)
+    for coeffs, check_w in [(a_iso, True), (a, False)]:
+        U, V, W = oracle.run(s, *coeffs, p.u0, p.v0, p.w0, p.steps)
+        assert U.min() >= 0 and U.max() <= 1 and V.min() >= 0 and V.max() <= 1
+        if check_w:
+            assert W.min() >= 0
+
+
+# --------------------------------------------------------------- 1D reduction and regimes
+
+def _oned_reference(U, V, W, a11, dx, dy, delta, rho, D, c, dt, n):
+    """Independent three-point 1D scheme (numpy), zero flux at both ends."""
+    U, V, W = U.copy(), V.copy(), W.copy()
+    for _ in range(n):
+        m = 1 - 0.5 * (U[1:] + U[:-1])
+        Hv = m * (V[1:] - V[:-1]) / dx ** 2
+        d1 = np.zeros_like(V)
+        d1[:-1] += Hv
+        d1[1:] -= Hv
+        Gw = 0.5 * (a11[1:] + a11[:-1]) * (W[1:] - W[:-1]) / dx ** 2
+        d2 = np.zeros_like(W)
+        d2[:-1] += Gw
+        d2[1:] -= Gw
+        U, V, W = (U + dt * (U * (1 - U) - delta * U * W),
+                   V + dt * (rho * V * (1 - V) + D * d1),
+                   W + dt * (c * (V - W) + d2))
+    return U, V, W
+
+
+def test_one_dimensional_reduction():
+    """y-uniform data with a y-independent diagonal tensor stays y-uniform
+    (exactly) and matches an independent 1D three-point scheme."""
+    nx, ny = 40, 6
+    x = (np.arange(nx) + 0.5) / nx
+    l1 = 0.2 + 0.8 * x ** 2
+    a11 = np.tile(l1, (ny, 1))
+    a22 = np.tile(0.3 + 0 * x, (ny, 1))
+    a12 = np.zeros((ny, nx))
+    U0 = np.tile(np.where(x < 0.2, 0.0, 1.0), (ny, 1))
+    V0 = 1 - U0
+    W0 = np.zeros((ny, nx))
+    s = oracle.Setup(nx, ny, 3.0, 1.0, 1e-3, 70.0, 2e-5)
+    U, V, W = oracle.run(s, a11, a12, a22, U0, V0, W0, 400)
+    for F in (U, V, W):
+        assert np.array_equal(F, np.tile(F[0], (ny, 1)))
+    Ur, Vr, Wr = _oned_reference(U0[0], V0[0], W0[0], l1, s.dx, s.dy, 3.0, 1.0, 1e-3, 70.0, 2e-5, 400)
+    assert np.max(np.abs(U[0] - Ur)) < 1e-13
+    assert np.max(np.abs(V[0] - Vr)) < 1e-13
+    assert np.max(np.abs(W[0] - Wr)) < 1e-13
+
+
+def _front_run(delta, nx=100, T=10.0, lam=1.0, D=4e-5, c=70.0, rho=1.0, xt=0.3):
+    x = (np.arange(nx) + 0.5) / nx
+    a = oracle.coefficients(np.zeros((1, nx)), np.full((1, nx), lam), np.full((1, nx), lam))
+    dt = oracle.stable_dt(nx, 1, *a, delta, rho, D, c)
+    s = oracle.Setup(nx, 1, delta, rho, D, c, dt)
+    U0 = np.ones((1, nx))
+    V0 = np.where(x < xt, 1.0, 0.0)[None, :]
+    U, V, W = oracle.run(s, *a, U0, V0, np.zeros((1, nx)), int(T / dt))
+    return x, U[0], V[0], W[0]
+
+
+def test_heterogeneous_invasion_regime():
+    """d < 1 (Section 2, item 1): tumour and normal cells coexist behind the
+    front, with U at the kinetic equilibrium 1 - d W of eq. (1)."""
+    x, U, V, W = _front_run(0.5)
+    bulk = x < 0.1
+    assert np.all(V[bulk] > 0.99)
+    assert np.all(U[bulk] > 0.4)
+    assert np.max(np.abs(U[bulk] - (1 - 0.5 * W[bulk]))) < 0.01
+
+
+def test_homogeneous_invasion_gap_regime():
+    """d > 1 (Section 2, item 2): healthy tissue is destroyed behind the front
+    and an interstitial gap (U and V both negligible) opens ahead of it."""
+    x, U, V, W = _front_run(12.5)
+    assert np.all(U[V > 0.5] < 1e-6)
+    gap = (U < 0.01) & (V < 0.01)
+    assert gap.sum() * (x[1] - x[0]) >= 0.05
+
+
+# --------------------------------------------------------------- diagnostics
+
+def test_diagnostics_definitions():
+    nx, ny = 9, 7
+    U, V, W = inputs.random_state(nx, ny, 91)
+    U[2, 3] = 0.001
+    V[2, 3] = 0.002
+    W[4, 4] = np.nan
+    d = oracle.diagnostics(U, V, W, 0.1, 0.2, eps=0.01)
+    assert d["nonfinite"] == 1
+    assert d["mass"][0] == pytest.approx(0.02 * U.sum(), rel=1e-14)
+    assert d["max"][1] == V.max() and d["min"][0] == U.min()
+    assert d["mass"][2] == pytest.approx(0.02 * np.nansum(W), rel=1e-14)
+    assert d["tumour_area"] == pytest.approx(0.02 * (V > 0.5).sum())
+    assert d["gap_area"] == pytest.approx(0.02 * ((U < 0.01) & (V < 0.01)).sum())
+
+
+# --------------------------------------------------------------- discrete adjoint
+
+def _problem_small(nx=12, ny=10, seed=101):
+    th, l1, l2 = inputs.heterogeneous_tensor(nx, ny, seed, 0.1, 1.0)
+    U, V, W = inputs.random_state(nx, ny, seed + 1)
+    s = oracle.Setup(nx, ny, 2.5, 1.3, 2e-3, 7.0, 0.0, lx=1.0, ly=0.9)
+    a = oracle.coefficients(th, l1, l2)
+    s.dt = 0.8 * oracle.stable_dt(nx, ny, *a, s.delta, s.rho, s.D, s.c, cfl=1.0, lx=1.0, ly=0.9)
+    return s, (th, l1, l2), a, (U, V, W)
+
+
+def test_one_step_adjoint_is_exact_transpose():
+    """One step is quadratic in the state and linear in (a11, a12, a22, delta,
+    rho, D, c), so central differences give its Jacobian exactly up to
+    rounding: <J dx, lam> must equal <dx, J^T lam> to ~1e-12."""
+    s, _, a, X = _problem_small()
+    ny, nx = X[0].shape
+    lam = [inputs.white_noise(nx, ny, 111 + k, -1, 1) for k in range(3)]
+    dX = [inputs.white_noise(nx, ny, 121 + k, -1, 1) for k in range(3)]
+    (lu, lv, lw), ga, gs = oracle.step_vjp(s, *a, *X, *lam)
+    eps = 1e-3
+
+    def F(Xs, A=a, ss=s):
+        return oracle.step(ss, *A, *Xs)
+
+    Fp = F([x + eps * d for x, d in zip(X, dX)])
+    Fm = F([x - eps * d for x, d in zip(X, dX)])
+    lhs = sum(np.sum((p - m) / (2 * eps) * l) for p, m, l in zip(Fp, Fm, lam))
+    rhs = sum(np.sum(d * g) for d, g in zip(dX, (lu, lv, lw)))
+    assert abs(lhs - rhs) <= 1e-11 * max(1.0, abs(lhs))
+    # coefficients
+    dA = [inputs.white_noise(nx, ny, 131 + k, -1, 1) for k in range(3)]
+    Fp = F(X, A=[x + eps * d for x, d in zip(a, dA)])
+    Fm = F(X, A=[x - eps * d for x, d in zip(a, dA)])
+    lhs = sum(np.sum((p - m) / (2 * eps) * l) for p, m, l in zip(Fp, Fm, lam))
+    rhs = sum(np.sum(d * g) for d, g in zip(dA, ga))
+    assert abs(lhs - rhs) <= 1e-11 * max(1.0, abs(lhs))
+    # scalars
+    for k, name in enumerate(["delta", "rho", "D", "c"]):
+        sp = oracle.Setup(**{**s.__dict__})
+        sm = oracle.Setup(**{**s.__dict__})
+        setattr(sp, name, getattr(s, name) + eps)
+        setattr(sm, name, getattr(s, name) - eps)
+        lhs = sum(np.sum((p - m) / (2 * eps) * l) for p, m, l in zip(F(X, ss=sp), F(X, ss=sm), lam))
+        assert abs(lhs - gs[k]) <= 1e-11 * max(1.0, abs(lhs))
+
+
+def test_adjoint_matches_finite_differences():
+    """Gradient of the final-state misfit over many steps against central
+    differences of the forward oracle (dt held fixed)."""
+    s, (th, l1, l2), a, X = _problem_small(nx=10, ny=9, seed=141)
+    n = 60
+    Vstar = inputs.random_state(s.nx, s.ny, 149)[1]
+
+    def loss(th_, l1_, l2_, ss=s):
+        A = oracle.coefficients(th_, l1_, l2_)
+        _, V, _ = oracle.run(ss, *A, *X, n)
+        return oracle.misfit(V, Vstar, ss.dx, ss.dy)
+
+    U, V, W = oracle.run(s, *a, *X, n)
+    gV = oracle.misfit_grad(V, Vstar, s.dx, s.dy)
+    _, ga, gs = oracle.adjoint(s, *a, *X, n, np.zeros_like(U), gV, np.zeros_like(W))
+    gth, gl1, gl2 = oracle.coefficients_vjp(th, l1, l2, *ga)
+    # the misfit is O(1e-2) and the tensor gradients O(1e-8): a large step keeps
+    # the rounding of the differences (~1e-16 L / eps) well below the tolerance;
+    # the O(eps^2) truncation error stays below it too.
+    eps = 1e-3
+    rng = np.random.default_rng(0)
+    cells = rng.choice(s.nx * s.ny, size=8, replace=False)
+    for field, grad in [(0, gth), (1, gl1), (2, gl2)]:
+        scale = np.max(np.abs(grad))
+        for k in cells:
+            args_p = [th.copy(), l1.copy(), l2.copy()]
+            args_m = [th.copy(), l1.copy(), l2.copy()]
+            args_p[field].flat[k] += eps
+            args_m[field].flat[k] -= eps
+            fd = (loss(*args_p) - loss(*args_m)) / (2 * eps)
+            assert abs(fd - grad.flat[k]) <= 1e-5 * scale
+    for k, name in enumerate(["delta", "rho", "D", "c"]):
+        sp = oracle.Setup(**{**s.__dict__})
+        sm = oracle.Setup(**{**s.__dict__})
+        h = 1e-4 * max(1.0, abs(getattr(s, name)))
+        setattr(sp, name, getattr(s, name) + h)
+        setattr(sm, name, getattr(s, name) - h)
+        fd = (loss(th, l1, l2, ss=sp) - loss(th, l1, l2, ss=sm)) / (2 * h)
+        assert abs(fd - gs[k]) <= 1e-5 * max(abs(fd), 1e-6)
+
+
+def test_coefficient_chain_rule_matches_finite_differences():
+    th = inputs.white_noise(6, 5, 151, 0, math.pi)
+    l1 = inputs.white_noise(6, 5, 152, 0.1, 1.0)
+    l2 = inputs.white_noise(6, 5, 153, 0.1, 1.0)
+    g = [inputs.white_noise(6, 5, 154 + k, -1, 1) for k in range(3)]
+    gt, g1, g2 = oracle.coefficients_vjp(th, l1, l2, *g)
+    eps = 1e-6
+    for which, grad in [(0, gt), (1, g1), (2, g2)]:
+        p = [th.copy(), l1.copy(), l2.copy()]
+        m = [th.copy(), l1.copy(), l2.copy()]
+        p[which] += eps
+        m[which] -= eps
+        Ap, Am = oracle.coefficients(*p), oracle.coefficients(*m)
+        fd = sum((x - y) / (2 * eps) * gg for x, y, gg in zip(Ap, Am, g))
+        assert np.max(np.abs(fd - grad)) < 1e-9
