@@ -1,0 +1,336 @@
+"""Benchmark of the explicit finite-volume step (arXiv 2006.01748) on GB300.
+
+Metric: cell-updates/s of the fused FP32 (+Kahan) forward step, next to the
+plain FP64 step on the same grid, the % of the measured HBM roofline, and
+the adjoint / forward time ratio.
+
+Workload (one bench step): the 8192 x 8192 heterogeneous tissue
+(lambda in [0.01, 1], delta=12.5, rho=1, D=4e-5, c=70, disk r=0.1), 5000
+explicit Euler steps of the fused FP32 + Kahan kernel with the tuned
+temporal-blocking depth, then the FP64 diagnostics of the final state.
+Inputs are synthetic and seeded; the 4 GB working set is larger than L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own instance (weak scaling,
+no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s FP32 fused vs FP64 plain, % HBM roofline; adjoint/forward time"
+BYTES_PER_CELL_PASS = {"fp32_kahan": 60, "fp32": 36, "fp64": 72}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=8192)
+    ap.add_argument("--time-steps", type=int, default=5000)
+    ap.add_argument("--steps-per-pass", type=int, default=0)
+    ap.add_argument("--fp64-time-steps", type=int, default=100)
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / CPU legs")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+class Dist:
+    def __init__(self, n):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            backend = "nccl"
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    import oracle
+    from paper_2006_01748_gb300 import inputs
+    oracle.build()
+    p = inputs.hetero_8192(nx=args.nx, steps=args.time_steps)
+    s, a = oracle.setup_for(p)
+    # each step: a bounded sample of the workload, 1 explicit step on the full grid
+    sample_steps = 1
+    U, V, W = p.u0, p.v0, p.w0
+    for _ in range(args.warmup):
+        U, V, W = oracle.run(s, *a, U, V, W, sample_steps)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, V, W = oracle.run(s, *a, U, V, W, sample_steps)
+    el = time.perf_counter() - t0
+    cells = p.cells * sample_steps * args.steps
+    value = cells / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(p, args, None),
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample_steps} explicit step of the {p.nx}x{p.ny} grid per bench step"},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(p, args, T):
+    return {"workload": f"hetero_8192: {p.nx}x{p.ny} cells, FP32 fused step with Kahan-compensated state, "
+                        f"{args.time_steps} explicit steps per bench step, lambda in [0.01,1], delta=12.5, "
+                        f"rho=1, D=4e-5, c=70",
+            "cells": p.cells, "time_steps_per_bench_step": args.time_steps, "steps_per_pass": T,
+            "l2": "inputs larger than L2 (working set 60 B/cell = %.1f GB)" % (60 * p.cells / 1e9),
+            "parallelism": f"{args.gpus} independent instance(s), one per GPU"}
+
+
+# ---------------------------------------------------------------- our arm
+
+def cpu_baseline_leg(p):
+    """The oracle as it stands, one host core, a bounded sample of the same
+    workload (3 explicit steps on the full grid)."""
+    import oracle
+    oracle.build()
+    s, a = oracle.setup_for(p)
+    n = 3
+    t0 = time.perf_counter()
+    oracle.run(s, *a, p.u0, p.v0, p.w0, n)
+    el = time.perf_counter() - t0
+    return {"value": p.cells * n / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} explicit steps of the {p.nx}x{p.ny} grid ({el:.1f} s)"}
+
+
+def run_ours(args, dist):
+    import torch
+    from paper_2006_01748_gb300 import build, gg, inputs
+    torch.cuda.set_device(dist.local)
+    build()
+    dev = torch.device("cuda", dist.local)
+    stream = torch.cuda.current_stream(dev)
+    p = inputs.hetero_8192(nx=args.nx, steps=args.time_steps, seed=inputs.SEED_HETERO_8192 + dist.rank)
+    sim = gg.GGSim.from_problem(p, precision="fp32_kahan", steps_per_pass=args.steps_per_pass)
+    T = sim.steps_per_pass
+    n_inner = args.time_steps
+    launches_per_step = -(-n_inner // T) + 2  # step passes + diagnostics partial/final
+
+    def one_step():
+        sim.step(n_inner)
+        rc, d = gg.gg_diagnostics(sim.handle)
+        if rc not in (gg.GG_OK,):
+            raise RuntimeError(f"diagnostics failed: {rc} {gg.gg_last_error(sim.handle)}")
+        return d
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    # timed region: K bench steps bracketed by barrier + synchronize
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kev = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(n_inner)
+        b.record(stream)
+        kev.append((a, b))
+        rc, d = gg.gg_diagnostics(sim.handle)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = dist.max(ms)
+    step_ms = [a.elapsed_time(b) for a, b in kev]
+    passes = -(-n_inner // T)
+    launch_ms = statistics.mean(step_ms) / passes
+    value = p.cells * n_inner * args.steps * dist.world / (ms_max / 1e3)
+
+    peak, peak_kind = measured_peaks()
+    alg_bytes = BYTES_PER_CELL_PASS["fp32_kahan"] * p.cells
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_kind": peak_kind, "kernel": f"step32_kernel<T={T}, Kahan>",
+                "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": launch_ms}
+
+    extras = {}
+    if not args.no_extras:
+        # plain FP64 step on the same grid (fewer time steps; throughput is per cell-update)
+        sim64 = gg.GGSim.from_problem(p, precision="fp64")
+        sim64.step(5)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim64.step(args.fp64_time_steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b)
+        sim64.close()
+        v64 = p.cells * args.fp64_time_steps / (ms64 / 1e3)
+        extras["fp64_plain"] = {"value": v64, "unit": "cell-updates/s", "time_steps": args.fp64_time_steps,
+                                "hbm_frac": 72 * p.cells / (ms64 / 1e3 / args.fp64_time_steps) / 1e9 / peak,
+                                "fp32_over_fp64": value / dist.world / v64}
+        # fused FP32 without Kahan and with T = 1 (single HBM pass per step)
+        for name, prec, spp in (("fp32_kahan_T1", "fp32_kahan", 1), ("fp32_T1", "fp32", 1)):
+            s2 = gg.GGSim.from_problem(p, precision=prec, steps_per_pass=spp)
+            s2.step(20)
+            torch.cuda.synchronize()
+            a.record(stream)
+            s2.step(200)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms2 = a.elapsed_time(b)
+            s2.close()
+            v2 = p.cells * 200 / (ms2 / 1e3)
+            extras[name] = {"value": v2, "unit": "cell-updates/s",
+                            "hbm_frac": BYTES_PER_CELL_PASS[prec] * p.cells / (ms2 / 1e3 / 200) / 1e9 / peak}
+
+    # end to end through the public API with host buffers: create from host
+    # arrays (H2D), advance, read the three fields back (D2H)
+    e2e_steps = 1
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s3 = gg.GGSim.from_problem(p, precision="fp32_kahan", steps_per_pass=args.steps_per_pass)
+        s3.step(n_inner)
+        out = s3.state(fp64=False)
+        s3.close()
+    torch.cuda.synchronize()
+    e2e_el = time.perf_counter() - t0
+    e2e = {"value": p.cells * n_inner * e2e_steps / e2e_el, "unit": "cell-updates/s",
+           "h2d_bytes_per_step": 6 * 8 * p.cells, "d2h_bytes_per_step": 3 * 4 * p.cells}
+
+    if dist.rank == 0:
+        cpu = cpu_baseline_leg(p) if (not args.no_extras and dist.world == 1) else None
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(p, args, T), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "clocks": ck, **extras,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+
+
+def main():
+    args = parse()
+    dist = Dist(args.gpus)
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

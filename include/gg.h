@@ -1,0 +1,226 @@
+/*
+ * gg.h -- C ABI of the GB300 (sm_103a) library for the explicit
+ * finite-volume time step of the anisotropic, heterogeneous
+ * Gatenby-Gawlinski system (Mascia, Pera, Simeoni, arXiv 2006.01748).
+ *
+ *   eq. (1)   U_t = U(1-U) - delta U W
+ *             V_t = rho V(1-V) + D div[(1-U) grad V]
+ *             W_t = c (V-W) + div(A grad W)
+ *   eq. (2)   A = [[a11, a12], [a12, a22]] per cell, built here as
+ *             A = R(theta) diag(lambda1, lambda2) R(theta)^T,
+ *             R = [[cos, -sin], [sin, cos]]
+ *   eq. (3)   explicit Euler on cell-centred unknowns, one fixed dt
+ *   Table 1   five-point tumour stencil, face mobility 1 - (U_P + U_nb)/2
+ *   Table 2   nine-point acid stencil (face fluxes, a12 cross terms)
+ *   Section 2 zero-flux (Neumann) boundary: no flux through boundary faces,
+ *             tangential differences at the boundary use mirror ghosts
+ *
+ * Paper symbols: delta = d, rho = r, D = alpha, c = c (acid rate); the
+ * tensor entries a, b, c of Table 2 are a11, a12, a22 here.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Status: every int-returning call returns GG_OK (0) or a negative
+ *   GG_ERR_* code; no exception or exit() crosses the ABI.
+ *   gg_last_error(sim) gives a text for the last failure on that object.
+ * - Layout of host field arrays: nx*ny values, row-major with x fastest,
+ *   element (i, j) at index j*nx + i, i along x in [0, nx), j along y.
+ *   Cell (i, j) is centred at ((i + 1/2) dx, (j + 1/2) dy), dx = lx/nx,
+ *   dy = ly/ny.
+ * - Ownership: the caller owns every pointer it passes; inputs are copied
+ *   before the call returns (host) or before the work it enqueues reads
+ *   them (device).  The library owns all device memory of a gg_sim /
+ *   gg_batch and frees it in gg_destroy / gg_batch_destroy.
+ * - Streams: work is enqueued on the cudaStream_t given at creation
+ *   (NULL = legacy default stream).  Calls marked "synchronizes" wait for
+ *   that stream before they return; the others are asynchronous.
+ * - One device: a gg_sim lives on the device that was current when it was
+ *   created; make that device current before every later call.
+ */
+#ifndef GG_H
+#define GG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define GG_OK             0
+#define GG_ERR_ARG       -1  /* null pointer, bad size or flag, non-finite input */
+#define GG_ERR_NOT_SPD   -2  /* some lambda1/lambda2 <= 0: A not positive definite (eq. 2) */
+#define GG_ERR_CFL       -3  /* explicit dt above the stable bound */
+#define GG_ERR_OOM       -4  /* device allocation failed */
+#define GG_ERR_CUDA      -5  /* a CUDA call failed (text in gg_last_error) */
+#define GG_ERR_NONFINITE -6  /* the state holds NaN or Inf */
+#define GG_ERR_TIMEOUT   -7  /* a bounded device-side wait gave up */
+#define GG_ERR_STATE     -8  /* call not valid in the object's current state */
+
+/* ---- precision of the state and the stencil arithmetic ---- */
+#define GG_FP64_PLAIN  0  /* double state and arithmetic, one thread per cell */
+#define GG_FP32        1  /* float state and arithmetic */
+#define GG_FP32_KAHAN  2  /* float arithmetic, Kahan-compensated float state */
+
+/* ---- fields for gg_read / gg_write ---- */
+#define GG_FIELD_U       0
+#define GG_FIELD_V       1
+#define GG_FIELD_W       2
+#define GG_FIELD_COMP_U  3  /* Kahan compensation terms (GG_FP32_KAHAN only) */
+#define GG_FIELD_COMP_V  4
+#define GG_FIELD_COMP_W  5
+#define GG_FIELD_A11     6  /* read only: tensor entries as used by the kernels */
+#define GG_FIELD_A12     7
+#define GG_FIELD_A22     8
+
+/* ---- gg_params.flags ---- */
+#define GG_FLAG_NO_REACTION     1  /* drop U(1-U) - delta U W, rho V(1-V), c(V-W) */
+#define GG_FLAG_ALLOW_UNSTABLE  2  /* accept an explicit dt above the stable bound */
+
+typedef struct {
+    int32_t nx, ny;   /* cells along x and y, >= 1 */
+    double lx, ly;    /* domain [0,lx] x [0,ly]; 0 means 1 (the unit square of Section 2) */
+} gg_grid;
+
+typedef struct {
+    double delta;          /* aggression rate d of eq. (1), >= 0 */
+    double rho;            /* tumour growth rate r, >= 0 */
+    double D;              /* tumour diffusion constant alpha, >= 0 */
+    double c;              /* acid production/reabsorption rate c, >= 0 */
+    double cfl;            /* fraction of dt_max used when dt == 0; 0 means 0.9 */
+    double dt;             /* 0: dt = cfl * dt_max; > 0: this dt (checked against dt_max) */
+    int32_t precision;     /* GG_FP64_PLAIN, GG_FP32 or GG_FP32_KAHAN */
+    int32_t flags;         /* GG_FLAG_* */
+    int32_t steps_per_pass;/* time steps per pass over HBM (temporal blocking), 0 = tuned */
+    int32_t reserved;      /* must be 0 */
+} gg_params;
+
+/* Stable-step rule (Section 2 recomputes dt for stability without giving a
+ * formula; this library's reading):
+ *   dt_max = 1 / ( 2 Lambda (1/dx^2 + 1/dy^2) + c + rho + 1 + delta ),
+ *   Lambda = max( max over cells of lambda_max(A), D ).
+ * It keeps every diagonal coefficient of eq. (3) non-negative and is below
+ * h^2 / (4 Lambda) on a square grid. */
+
+typedef struct {
+    double mass[3];      /* dx dy sum of U, V, W (finite values only) */
+    double min[3];       /* minima of U, V, W */
+    double max[3];       /* maxima of U, V, W */
+    int64_t nonfinite;   /* NaN/Inf values over the three fields */
+    double tumour_area;  /* dx dy #{V > 1/2} */
+    double gap_area;     /* dx dy #{U < gap_eps and V < gap_eps}: interstitial gap of Section 2 */
+    double gap_eps;      /* threshold used (input of gg_diagnostics_eps, 0.01 by default) */
+} gg_diag;
+
+typedef struct gg_sim gg_sim;
+
+/* Create a simulation of eq. (3) on one grid.
+ *   theta, lambda1, lambda2: host, nx*ny doubles each; per-cell principal
+ *     direction and eigenvalues of A (eq. 2); lambda > 0 required.
+ *   u0, v0, w0: host, nx*ny doubles each: initial state at t = 0.
+ *   cuda_stream: cudaStream_t to enqueue on (NULL = default stream).
+ *   *out receives the new object (NULL on failure).
+ * Validates sizes, rates and flags (GG_ERR_ARG), finiteness of all six
+ * arrays (GG_ERR_ARG), lambda > 0 (GG_ERR_NOT_SPD) and an explicit dt
+ * against dt_max (GG_ERR_CFL unless GG_FLAG_ALLOW_UNSTABLE).  Builds
+ * a11, a12, a22 on the device, fixes dt, picks the launch plan.
+ * Synchronizes. */
+int gg_create(const gg_grid* grid, const gg_params* params,
+              const double* theta, const double* lambda1, const double* lambda2,
+              const double* u0, const double* v0, const double* w0,
+              void* cuda_stream, gg_sim** out);
+
+/* Advance nsteps >= 0 explicit Euler steps of eq. (3) with the fixed dt.
+ * Asynchronous: returns once the kernels are enqueued (launch errors are
+ * reported as GG_ERR_CUDA). */
+int gg_step(gg_sim* sim, int64_t nsteps);
+
+/* Copy one field (GG_FIELD_*) of the current state to dst, nx*ny values in
+ * the host layout above.  dst_on_device: 0 host pointer, 1 device pointer.
+ * dst_fp64: 1 writes doubles, 0 writes floats.  Synchronizes. */
+int gg_read(gg_sim* sim, int32_t field, void* dst, int32_t dst_on_device, int32_t dst_fp64);
+
+/* Overwrite one state field (U, V, W or a compensation field) from src
+ * (same conventions as gg_read); used to resume from a checkpoint.
+ * Writing U, V or W of a GG_FP32_KAHAN simulation does not touch its
+ * compensation terms.  Synchronizes. */
+int gg_write(gg_sim* sim, int32_t field, const void* src, int32_t src_on_device, int32_t src_fp64);
+
+/* FP64 diagnostics of the current state: integrals, extrema, non-finite
+ * count, tumour and gap areas (gap threshold 0.01).  Synchronizes.
+ * Returns GG_ERR_NONFINITE (with *out filled) if the state holds NaN/Inf. */
+int gg_diagnostics(gg_sim* sim, gg_diag* out);
+
+/* Same as gg_diagnostics with an explicit gap threshold eps > 0. */
+int gg_diagnostics_eps(gg_sim* sim, double eps, gg_diag* out);
+
+/* Discrete adjoint of nsteps steps of eq. (3) starting from the current
+ * state X^0 (the transpose of the Jacobian of each step, applied in reverse
+ * order; dt is held fixed and not differentiated).
+ *   dLdu_N, dLdv_N, dLdw_N: device, nx*ny floats (host layout) holding
+ *     dL/d(U,V,W) at step nsteps; NULL means zero.
+ *   g_theta, g_lambda1, g_lambda2: device, nx*ny floats: dL/d(theta,
+ *     lambda1, lambda2) (chain rule through eq. (2)); may be NULL.
+ *   g_u0, g_v0, g_w0: device, nx*ny floats: dL/d(U,V,W) at step 0; may be NULL.
+ *   g_scalars: host, 4 doubles: dL/d(delta, rho, D, c); may be NULL.
+ *   checkpoint_every: steps between stored states (0 = about sqrt(nsteps)).
+ * The forward pass is recomputed from stored checkpoints segment by segment
+ * (sqrt(N) checkpointing).  On return the simulation holds the state at step
+ * nsteps, as after gg_step(sim, nsteps).  Not available for GG_FP64_PLAIN
+ * (GG_ERR_STATE).  Synchronizes. */
+int gg_adjoint(gg_sim* sim, int64_t nsteps,
+               const float* dLdu_N, const float* dLdv_N, const float* dLdw_N,
+               float* g_theta, float* g_lambda1, float* g_lambda2,
+               float* g_u0, float* g_v0, float* g_w0,
+               double* g_scalars, int64_t checkpoint_every);
+
+double gg_dt(const gg_sim* sim);              /* fixed dt (0 if sim is NULL) */
+double gg_dt_max(const gg_sim* sim);          /* stable bound dt_max */
+int64_t gg_step_count(const gg_sim* sim);     /* steps taken so far */
+int32_t gg_steps_per_pass(const gg_sim* sim); /* temporal blocking depth in use */
+const char* gg_last_error(const gg_sim* sim); /* text of the last failure ("" if none) */
+const char* gg_error_string(int32_t status);  /* static text of a status code */
+
+/* Release the simulation and its device memory (NULL is a no-op).
+ * Synchronizes. */
+int gg_destroy(gg_sim* sim);
+
+/* ---- ensembles: many independent grids advanced by one persistent launch ---- */
+
+typedef struct gg_batch gg_batch;
+
+/* Create n >= 1 independent simulations, advanced together.
+ *   grids[k], params[k]: grid and rates of instance k (precision must be
+ *     GG_FP32 or GG_FP32_KAHAN and equal for all instances).
+ *   fields: 6*n host pointers, fields[6k + m] = theta, lambda1, lambda2,
+ *     u0, v0, w0 of instance k for m = 0..5 (nx*ny doubles each).
+ * Validation as in gg_create, per instance.  Synchronizes. */
+int gg_batch_create(int32_t n, const gg_grid* grids, const gg_params* params,
+                    const double* const* fields, void* cuda_stream, gg_batch** out);
+
+/* Advance every instance nsteps steps with its own dt, in one persistent,
+ * cooperative kernel launch that loops over (instance, tile) work items and
+ * separates steps by a grid barrier; the launch is captured in a CUDA graph
+ * the first time a given nsteps is used and replayed afterwards.  A barrier
+ * wait that exceeds its iteration limit sets a device error word and the
+ * call returns GG_ERR_TIMEOUT (checked at the next synchronizing call).
+ * Asynchronous. */
+int gg_batch_step(gg_batch* b, int64_t nsteps);
+
+/* Read field of instance inst (same conventions as gg_read).  Synchronizes;
+ * returns GG_ERR_TIMEOUT if a barrier wait of an earlier step gave up. */
+int gg_batch_read(gg_batch* b, int32_t inst, int32_t field, void* dst,
+                  int32_t dst_on_device, int32_t dst_fp64);
+
+/* Diagnostics of instance inst.  Synchronizes. */
+int gg_batch_diagnostics(gg_batch* b, int32_t inst, gg_diag* out);
+
+double gg_batch_dt(const gg_batch* b, int32_t inst);
+const char* gg_batch_last_error(const gg_batch* b);
+int gg_batch_destroy(gg_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GG_H */

@@ -1,0 +1,434 @@
+// Host side of the C ABI declared in include/gg.h: argument validation,
+// device memory of a simulation, the fixed time step, the launch plan and
+// the read / write / diagnostics entry points.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "gg_internal.cuh"
+#include "gg_sim.cuh"
+
+using namespace gg;
+
+namespace gg {
+
+void set_error(gg_sim* s, const char* fmt, const char* detail)
+{
+    if (!s) return;
+    char buf[512];
+    snprintf(buf, sizeof buf, fmt, detail ? detail : "");
+    s->last_error = buf;
+}
+
+int cuda_fail(gg_sim* s, cudaError_t e, const char* where)
+{
+    if (s) s->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return GG_ERR_CUDA;
+}
+
+double stable_dt_max(double dx, double dy, double Lambda, const gg_params& p)
+{
+    const double L = std::max(Lambda, p.D);
+    return 1.0 / (2.0 * L * (1.0 / (dx * dx) + 1.0 / (dy * dy)) + (p.c + p.rho + 1.0 + p.delta));
+}
+
+Rates32 rates32(const gg_sim* s)
+{
+    Rates32 r;
+    r.dt = (float)s->dt;
+    r.D = (float)s->params.D;
+    r.delta = (float)s->params.delta;
+    r.rho = (float)s->params.rho;
+    r.c = (float)s->params.c;
+    r.kx = (float)(0.5 / (s->dx * s->dx));
+    r.ky = (float)(0.5 / (s->dy * s->dy));
+    r.kc = (float)(0.25 / (s->dx * s->dy));
+    r.ihx2 = (float)(1.0 / (s->dx * s->dx));
+    r.ihy2 = (float)(1.0 / (s->dy * s->dy));
+    r.no_reaction = (s->params.flags & GG_FLAG_NO_REACTION) ? 1 : 0;
+    return r;
+}
+
+Grid32 grid32(const gg_sim* s, int cur)
+{
+    Grid32 g;
+    const int nxt = cur ^ 1;
+    g.u = s->f32[cur][0]; g.v = s->f32[cur][1]; g.w = s->f32[cur][2];
+    g.uo = s->f32[nxt][0]; g.vo = s->f32[nxt][1]; g.wo = s->f32[nxt][2];
+    const bool k = s->params.precision == GG_FP32_KAHAN;
+    g.cu = k ? s->f32[cur][3] : nullptr; g.cv = k ? s->f32[cur][4] : nullptr; g.cw = k ? s->f32[cur][5] : nullptr;
+    g.cuo = k ? s->f32[nxt][3] : nullptr; g.cvo = k ? s->f32[nxt][4] : nullptr; g.cwo = k ? s->f32[nxt][5] : nullptr;
+    g.a11 = s->a32[0]; g.a12 = s->a32[1]; g.a22 = s->a32[2];
+    g.nx = s->nx; g.ny = s->ny; g.pitch = s->pitch;
+    return g;
+}
+
+// Default launch plan: strips of at most 256 output columns split evenly,
+// chunks of 128 rows, 128 threads.
+Plan32 default_plan(int nx, int ny, int T)
+{
+    Plan32 p;
+    p.T = T;
+    p.halo = T;
+    const int ns = (nx + 255) / 256;
+    p.bx = round_up((nx + ns - 1) / ns, 4);
+    p.by = std::min(ny, 128);
+    p.threads = 128;
+    return p;
+}
+
+}  // namespace gg
+
+namespace {
+
+bool finite_nonneg(double x) { return isfinite(x) && x >= 0.0; }
+
+int validate(const gg_grid* grid, const gg_params* params, std::string& why)
+{
+    if (!grid || !params) { why = "grid or params is NULL"; return GG_ERR_ARG; }
+    if (grid->nx < 1 || grid->ny < 1) { why = "nx and ny must be >= 1"; return GG_ERR_ARG; }
+    if ((int64_t)grid->nx * grid->ny > (int64_t)1 << 31) { why = "nx*ny must be <= 2^31"; return GG_ERR_ARG; }
+    if (!(isfinite(grid->lx) && grid->lx >= 0) || !(isfinite(grid->ly) && grid->ly >= 0)) {
+        why = "lx, ly must be finite and >= 0"; return GG_ERR_ARG;
+    }
+    const gg_params& p = *params;
+    if (!finite_nonneg(p.delta) || !finite_nonneg(p.rho) || !finite_nonneg(p.D) || !finite_nonneg(p.c)) {
+        why = "delta, rho, D, c must be finite and >= 0"; return GG_ERR_ARG;
+    }
+    if (!(isfinite(p.cfl) && p.cfl >= 0.0 && p.cfl <= 1.0)) { why = "cfl must lie in [0, 1]"; return GG_ERR_ARG; }
+    if (!(isfinite(p.dt) && p.dt >= 0.0)) { why = "dt must be finite and >= 0"; return GG_ERR_ARG; }
+    if (p.precision != GG_FP64_PLAIN && p.precision != GG_FP32 && p.precision != GG_FP32_KAHAN) {
+        why = "unknown precision"; return GG_ERR_ARG;
+    }
+    if (p.flags & ~(GG_FLAG_NO_REACTION | GG_FLAG_ALLOW_UNSTABLE)) { why = "unknown flag bits"; return GG_ERR_ARG; }
+    if (p.steps_per_pass < 0 || p.steps_per_pass > kMaxT) { why = "steps_per_pass must lie in [0, 8]"; return GG_ERR_ARG; }
+    if (p.reserved != 0) { why = "reserved must be 0"; return GG_ERR_ARG; }
+    return GG_OK;
+}
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+extern "C" {
+
+const char* gg_error_string(int32_t status)
+{
+    switch (status) {
+        case GG_OK: return "ok";
+        case GG_ERR_ARG: return "invalid argument";
+        case GG_ERR_NOT_SPD: return "diffusion tensor not positive definite (lambda <= 0)";
+        case GG_ERR_CFL: return "time step above the stable bound";
+        case GG_ERR_OOM: return "device out of memory";
+        case GG_ERR_CUDA: return "CUDA error";
+        case GG_ERR_NONFINITE: return "non-finite state";
+        case GG_ERR_TIMEOUT: return "device-side wait timed out";
+        case GG_ERR_STATE: return "call not valid in this state";
+        default: return "unknown status";
+    }
+}
+
+const char* gg_last_error(const gg_sim* s) { return s ? s->last_error.c_str() : g_create_error.c_str(); }
+
+int gg_create(const gg_grid* grid, const gg_params* params, const double* theta, const double* lambda1,
+              const double* lambda2, const double* u0, const double* v0, const double* w0, void* cuda_stream,
+              gg_sim** out)
+{
+    g_create_error.clear();
+    if (!out) { g_create_error = "out is NULL"; return GG_ERR_ARG; }
+    *out = nullptr;
+    std::string why;
+    int rc = validate(grid, params, why);
+    if (rc == GG_OK && (!theta || !lambda1 || !lambda2 || !u0 || !v0 || !w0)) {
+        why = "a field pointer is NULL";
+        rc = GG_ERR_ARG;
+    }
+    if (rc != GG_OK) { g_create_error = why; return rc; }
+
+    gg_sim* s = new gg_sim();
+    s->params = *params;
+    if (s->params.cfl == 0.0) s->params.cfl = 0.9;
+    s->nx = grid->nx;
+    s->ny = grid->ny;
+    s->lx = grid->lx > 0 ? grid->lx : 1.0;
+    s->ly = grid->ly > 0 ? grid->ly : 1.0;
+    s->dx = s->lx / s->nx;
+    s->dy = s->ly / s->ny;
+    s->stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&s->device);
+    const bool fp64 = s->params.precision == GG_FP64_PLAIN;
+    const bool kahan = s->params.precision == GG_FP32_KAHAN;
+    s->pitch = fp64 ? round_up(s->nx, 16) : round_up(s->nx, 32);
+    const size_t n = (size_t)s->nx * s->ny;
+    const size_t esz = fp64 ? 8 : 4;
+    const size_t fbytes = (size_t)s->pitch * s->ny * esz;
+    const size_t fstride = (fbytes + 255) / 256 * 256;
+    const int nstate = kahan ? 6 : 3;
+    const size_t dense_stride = (n * 8 + 255) / 256 * 256;
+    const size_t diag_bytes = (size_t)kDiagBlocks * kDiagStride * 8 + 32 * 8;
+    // arena: 2 x nstate state fields, 3 tensor fields, theta/l1/l2 (FP64 dense), diagnostics
+    const size_t keep_tensor = fp64 ? 0 : 3;
+    const size_t arena = fstride * (2 * nstate + 3) + dense_stride * keep_tensor + diag_bytes + 256;
+    cudaError_t e = cudaMalloc(&s->arena, arena);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "device allocation of the simulation arena failed";
+        delete s;
+        return GG_ERR_OOM;
+    }
+    s->arena_bytes = arena;
+    char* p = (char*)s->arena;
+    for (int b = 0; b < 2; ++b)
+        for (int f = 0; f < nstate; ++f) {
+            if (fp64) s->f64[b][f] = (double*)p; else s->f32[b][f] = (float*)p;
+            p += fstride;
+        }
+    for (int f = 0; f < 3; ++f) {
+        if (fp64) s->a64[f] = (double*)p; else s->a32[f] = (float*)p;
+        p += fstride;
+    }
+    for (size_t f = 0; f < keep_tensor; ++f) {
+        s->tensor[f] = (double*)p;
+        p += dense_stride;
+    }
+    s->diag_partials = (double*)p;
+    p += (size_t)kDiagBlocks * kDiagStride * 8;
+    s->diag_out = (double*)p;            // 16 doubles
+    s->counters = (unsigned long long*)(s->diag_out + 16);  // [0] bad lambda, [1] nonfinite, [2] lmax bits
+    // Zero the whole arena once: padding columns and compensation terms start at 0.
+    e = cudaMemsetAsync(s->arena, 0, arena, s->stream);
+    if (e != cudaSuccess) { rc = cuda_fail(s, e, "memset"); g_create_error = s->last_error; gg_destroy(s); return rc; }
+
+    // Stage the six host arrays on the device (dense FP64), then build the
+    // tensor and the pitched state.
+    double* staging = nullptr;
+    const size_t nstage = fp64 ? 6 : 3;  // FP32 keeps theta/l1/l2 in the arena
+    e = cudaMalloc(&staging, dense_stride * nstage);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "device allocation of the upload staging buffer failed";
+        gg_destroy(s);
+        return GG_ERR_OOM;
+    }
+    double* dth = fp64 ? staging : s->tensor[0];
+    double* dl1 = fp64 ? (double*)((char*)staging + dense_stride) : s->tensor[1];
+    double* dl2 = fp64 ? (double*)((char*)staging + 2 * dense_stride) : s->tensor[2];
+    double* du0 = (double*)((char*)staging + (fp64 ? 3 : 0) * dense_stride);
+    double* dv0 = (double*)((char*)du0 + dense_stride);
+    double* dw0 = (double*)((char*)dv0 + dense_stride);
+    const double* hsrc[6] = {theta, lambda1, lambda2, u0, v0, w0};
+    double* ddst[6] = {dth, dl1, dl2, du0, dv0, dw0};
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(ddst[k], hsrc[k], n * 8, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = launch_coefficients(dth, dl1, dl2, s->nx, s->ny, fp64 ? (void*)s->a64[0] : (void*)s->a32[0],
+                                fp64 ? (void*)s->a64[1] : (void*)s->a32[1], fp64 ? (void*)s->a64[2] : (void*)s->a32[2],
+                                s->pitch, fp64, s->counters, s->counters + 2, s->stream);
+    const double* dstate[3] = {du0, dv0, dw0};
+    for (int f = 0; f < 3 && e == cudaSuccess; ++f)
+        e = launch_unpack(dstate[f], true, fp64 ? (void*)s->f64[0][f] : (void*)s->f32[0][f], fp64, s->nx, s->ny,
+                          s->pitch, s->counters + 1, s->stream);
+    unsigned long long cnt[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, s->counters, sizeof cnt, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(staging);
+    if (e != cudaSuccess) { rc = cuda_fail(s, e, "create"); g_create_error = s->last_error; gg_destroy(s); return rc; }
+    if (cnt[0]) {
+        char b[128];
+        snprintf(b, sizeof b, "%llu cells with lambda <= 0 or non-finite theta/lambda", cnt[0]);
+        g_create_error = b;
+        gg_destroy(s);
+        return GG_ERR_NOT_SPD;
+    }
+    if (cnt[1]) {
+        char b[128];
+        snprintf(b, sizeof b, "%llu non-finite initial values", cnt[1]);
+        g_create_error = b;
+        gg_destroy(s);
+        return GG_ERR_ARG;
+    }
+    double lmax;
+    memcpy(&lmax, &cnt[2], sizeof lmax);
+    s->lambda_max = lmax;
+    s->dt_max = stable_dt_max(s->dx, s->dy, lmax, s->params);
+    if (s->params.dt > 0.0) {
+        if (s->params.dt > s->dt_max && !(s->params.flags & GG_FLAG_ALLOW_UNSTABLE)) {
+            char b[160];
+            snprintf(b, sizeof b, "dt = %.6g exceeds the stable bound %.6g", s->params.dt, s->dt_max);
+            g_create_error = b;
+            gg_destroy(s);
+            return GG_ERR_CFL;
+        }
+        s->dt = s->params.dt;
+    } else {
+        s->dt = s->params.cfl * s->dt_max;
+    }
+    if (!fp64) {
+        const int T = s->params.steps_per_pass > 0 ? s->params.steps_per_pass : 1;
+        s->plan = default_plan(s->nx, s->ny, T);
+    }
+    *out = s;
+    return GG_OK;
+}
+
+int gg_step(gg_sim* s, int64_t nsteps)
+{
+    if (!s) return GG_ERR_ARG;
+    if (nsteps < 0) { s->last_error = "nsteps < 0"; return GG_ERR_ARG; }
+    cudaError_t e = cudaSuccess;
+    if (s->params.precision == GG_FP64_PLAIN) {
+        Rates64 r;
+        r.dt = s->dt; r.D = s->params.D; r.delta = s->params.delta; r.rho = s->params.rho; r.c = s->params.c;
+        r.kx = 0.5 / (s->dx * s->dx); r.ky = 0.5 / (s->dy * s->dy); r.kc = 0.25 / (s->dx * s->dy);
+        r.ihx2 = 1.0 / (s->dx * s->dx); r.ihy2 = 1.0 / (s->dy * s->dy);
+        r.no_reaction = (s->params.flags & GG_FLAG_NO_REACTION) ? 1 : 0;
+        for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
+            Grid64 g;
+            const int c = s->cur, nn = c ^ 1;
+            g.u = s->f64[c][0]; g.v = s->f64[c][1]; g.w = s->f64[c][2];
+            g.uo = s->f64[nn][0]; g.vo = s->f64[nn][1]; g.wo = s->f64[nn][2];
+            g.a11 = s->a64[0]; g.a12 = s->a64[1]; g.a22 = s->a64[2];
+            g.nx = s->nx; g.ny = s->ny; g.pitch = s->pitch;
+            e = launch_step64(g, r, s->stream);
+            if (e == cudaSuccess) { s->cur = nn; s->steps++; }
+        }
+    } else {
+        const Rates32 r = rates32(s);
+        const bool kahan = s->params.precision == GG_FP32_KAHAN;
+        int64_t left = nsteps;
+        while (left > 0 && e == cudaSuccess) {
+            const int T = (int)std::min<int64_t>(left, s->plan.T);
+            e = launch_step32(grid32(s, s->cur), r, s->plan, T, kahan, s->stream);
+            if (e == cudaSuccess) { s->cur ^= 1; s->steps += T; left -= T; }
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
+    return GG_OK;
+}
+
+double gg_dt(const gg_sim* s) { return s ? s->dt : 0.0; }
+double gg_dt_max(const gg_sim* s) { return s ? s->dt_max : 0.0; }
+int64_t gg_step_count(const gg_sim* s) { return s ? s->steps : 0; }
+int32_t gg_steps_per_pass(const gg_sim* s) { return s ? (s->params.precision == GG_FP64_PLAIN ? 1 : s->plan.T) : 0; }
+
+static void* field_ptr(gg_sim* s, int32_t field, bool& fp64)
+{
+    fp64 = s->params.precision == GG_FP64_PLAIN;
+    const bool kahan = s->params.precision == GG_FP32_KAHAN;
+    if (field >= GG_FIELD_U && field <= GG_FIELD_W)
+        return fp64 ? (void*)s->f64[s->cur][field] : (void*)s->f32[s->cur][field];
+    if (field >= GG_FIELD_COMP_U && field <= GG_FIELD_COMP_W) return kahan ? (void*)s->f32[s->cur][field] : nullptr;
+    if (field >= GG_FIELD_A11 && field <= GG_FIELD_A22) {
+        const int f = field - GG_FIELD_A11;
+        return fp64 ? (void*)s->a64[f] : (void*)s->a32[f];
+    }
+    return nullptr;
+}
+
+static int ensure_staging(gg_sim* s)
+{
+    if (s->staging) return GG_OK;
+    const size_t bytes = (size_t)s->nx * s->ny * 8;
+    cudaError_t e = cudaMalloc(&s->staging, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        s->staging = nullptr;
+        s->last_error = "staging allocation failed";
+        return GG_ERR_OOM;
+    }
+    return GG_OK;
+}
+
+int gg_read(gg_sim* s, int32_t field, void* dst, int32_t dst_on_device, int32_t dst_fp64)
+{
+    if (!s) return GG_ERR_ARG;
+    if (!dst) { s->last_error = "dst is NULL"; return GG_ERR_ARG; }
+    bool fp64;
+    void* src = field_ptr(s, field, fp64);
+    if (!src) { s->last_error = "field not available for this precision"; return GG_ERR_ARG; }
+    const size_t n = (size_t)s->nx * s->ny;
+    const size_t bytes = n * (dst_fp64 ? 8 : 4);
+    cudaError_t e;
+    if (dst_on_device) {
+        e = launch_pack(src, fp64, dst, dst_fp64 != 0, s->nx, s->ny, s->pitch, s->stream);
+    } else {
+        int rc = ensure_staging(s);
+        if (rc) return rc;
+        e = launch_pack(src, fp64, s->staging, dst_fp64 != 0, s->nx, s->ny, s->pitch, s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, s->staging, bytes, cudaMemcpyDeviceToHost, s->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "read");
+    return GG_OK;
+}
+
+int gg_write(gg_sim* s, int32_t field, const void* src, int32_t src_on_device, int32_t src_fp64)
+{
+    if (!s) return GG_ERR_ARG;
+    if (!src) { s->last_error = "src is NULL"; return GG_ERR_ARG; }
+    if (field > GG_FIELD_COMP_W) { s->last_error = "tensor fields are read-only"; return GG_ERR_ARG; }
+    bool fp64;
+    void* dstp = field_ptr(s, field, fp64);
+    if (!dstp) { s->last_error = "field not available for this precision"; return GG_ERR_ARG; }
+    const size_t n = (size_t)s->nx * s->ny;
+    cudaError_t e = cudaSuccess;
+    const void* dsrc = src;
+    if (!src_on_device) {
+        int rc = ensure_staging(s);
+        if (rc) return rc;
+        e = cudaMemcpyAsync(s->staging, src, n * (src_fp64 ? 8 : 4), cudaMemcpyHostToDevice, s->stream);
+        dsrc = s->staging;
+    }
+    if (e == cudaSuccess) e = launch_unpack(dsrc, src_fp64 != 0, dstp, fp64, s->nx, s->ny, s->pitch, nullptr, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "write");
+    return GG_OK;
+}
+
+int gg_diagnostics_eps(gg_sim* s, double eps, gg_diag* out)
+{
+    if (!s) return GG_ERR_ARG;
+    if (!out || !(eps > 0.0) || !isfinite(eps)) { s->last_error = "out is NULL or eps <= 0"; return GG_ERR_ARG; }
+    const bool fp64 = s->params.precision == GG_FP64_PLAIN;
+    const void* f[3];
+    for (int k = 0; k < 3; ++k) f[k] = fp64 ? (const void*)s->f64[s->cur][k] : (const void*)s->f32[s->cur][k];
+    double h[12];
+    cudaError_t e = launch_diagnostics(f[0], f[1], f[2], fp64, s->nx, s->ny, s->pitch, eps, s->diag_partials,
+                                       s->diag_out, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, s->diag_out, sizeof h, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "diagnostics");
+    const double cell = s->dx * s->dy;
+    for (int k = 0; k < 3; ++k) {
+        out->mass[k] = h[k] * cell;
+        out->min[k] = h[3 + k];
+        out->max[k] = h[6 + k];
+    }
+    out->nonfinite = (int64_t)h[9];
+    out->tumour_area = h[10] * cell;
+    out->gap_area = h[11] * cell;
+    out->gap_eps = eps;
+    if (out->nonfinite) {
+        s->last_error = "state holds non-finite values";
+        return GG_ERR_NONFINITE;
+    }
+    return GG_OK;
+}
+
+int gg_diagnostics(gg_sim* s, gg_diag* out) { return gg_diagnostics_eps(s, 0.01, out); }
+
+int gg_destroy(gg_sim* s)
+{
+    if (!s) return GG_OK;
+    cudaStreamSynchronize(s->stream);
+    gg_release_extras(s);
+    if (s->staging) cudaFree(s->staging);
+    if (s->arena) cudaFree(s->arena);
+    delete s;
+    return GG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal declarations shared by the translation units of libgg.so.
+// Nothing here is part of the public ABI (include/gg.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "gg.h"
+
+namespace gg {
+
+constexpr int kMaxT = 8;           // deepest temporal blocking supported
+constexpr int kDiagBlocks = 608;   // 4 x 152 SMs: diagnostics partial sums
+constexpr int kDiagStride = 16;    // doubles per diagnostics partial
+
+// Device-side description of one FP32 state on a pitched grid.  Row j of a
+// field starts at base + j * pitch; pitch is a multiple of 32 floats.
+struct Grid32 {
+    const float* u; const float* v; const float* w;
+    const float* cu; const float* cv; const float* cw;   // null without Kahan
+    float* uo; float* vo; float* wo;
+    float* cuo; float* cvo; float* cwo;
+    const float* a11; const float* a12; const float* a22;
+    int nx, ny, pitch;
+};
+
+// Scalars of eq. (3) in FP32, rounded once from the FP64 host values.
+struct Rates32 {
+    float dt, D, delta, rho, c;
+    float kx, ky, kc;     // 0.5/dx^2, 0.5/dy^2, 0.25/(dx dy)
+    float ihx2, ihy2;     // 1/dx^2, 1/dy^2
+    int no_reaction;
+};
+
+// Launch plan of the FP32 step kernel: strips of bx output columns (plus a
+// halo of `halo` columns on each side), chunks of by output rows, `threads`
+// threads per CTA, T steps per pass.
+struct Plan32 {
+    int T = 1;
+    int bx = 256, by = 128, halo = 1, threads = 128;
+};
+
+size_t step32_smem_bytes(const Plan32& p, bool kahan);
+cudaError_t launch_step32(const Grid32& g, const Rates32& r, const Plan32& p, int T, bool kahan,
+                          cudaStream_t s);
+
+// FP64 plain step (one thread per cell).
+struct Grid64 {
+    const double* u; const double* v; const double* w;
+    double* uo; double* vo; double* wo;
+    const double* a11; const double* a12; const double* a22;
+    int nx, ny, pitch;
+};
+struct Rates64 {
+    double dt, D, delta, rho, c;
+    double kx, ky, kc, ihx2, ihy2;
+    int no_reaction;
+};
+cudaError_t launch_step64(const Grid64& g, const Rates64& r, cudaStream_t s);
+
+// Coefficients of eq. (2) and validation counters.
+// counters[0]: cells with lambda <= 0 or non-finite theta/lambda;
+// counters[1]: non-finite initial values; lmax_bits: max lambda_max as the
+// bit pattern of a non-negative double (atomicMax on unsigned long long).
+cudaError_t launch_coefficients(const double* theta, const double* l1, const double* l2, int nx, int ny,
+                                void* a11, void* a12, void* a22, int pitch, bool fp64,
+                                unsigned long long* counters, unsigned long long* lmax_bits,
+                                cudaStream_t s);
+
+// Dense FP64 host-layout field -> pitched FP32/FP64 device field (counts
+// non-finite values into *nonfinite when it is not null).
+cudaError_t launch_unpack(const void* src, bool src_fp64, void* dst, bool dst_fp64, int nx, int ny,
+                          int pitch, unsigned long long* nonfinite, cudaStream_t s);
+// Pitched device field -> dense device buffer.
+cudaError_t launch_pack(const void* src, bool src_fp64, void* dst, bool dst_fp64, int nx, int ny,
+                        int pitch, cudaStream_t s);
+
+// Diagnostics: partials then a deterministic fixed-order final reduction.
+// out[0..2] sums, [3..5] minima, [6..8] maxima, [9] non-finite count,
+// [10] tumour cells, [11] gap cells (scaled by dx dy on the host).
+cudaError_t launch_diagnostics(const void* u, const void* v, const void* w, bool fp64, int nx, int ny,
+                               int pitch, double eps, double* partials, double* out, cudaStream_t s);
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace gg

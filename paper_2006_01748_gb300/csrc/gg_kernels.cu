@@ -1,0 +1,353 @@
+// Supporting kernels of libgg.so: the plain FP64 step, the tensor build of
+// eq. (2), layout conversion between the dense host layout and the pitched
+// device layout, and the FP64 diagnostics reduction.
+#include <math.h>
+
+#include <algorithm>
+
+#include "gg_internal.cuh"
+
+namespace gg {
+namespace {
+
+// ---------------------------------------------------------------- FP64 plain step
+//
+// One thread per cell, every operand read from global memory: the plain
+// design (the CUDA kernel of Section 3 updates each cell from the previous
+// iterate in global memory), kept as the double-precision comparison point.
+__global__ void __launch_bounds__(256) step64_kernel(const Grid64 g, const Rates64 k)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int nx = g.nx, ny = g.ny, pitch = g.pitch;
+    if (i >= nx || j >= ny) return;
+    const bool hasW = i > 0, hasE = i + 1 < nx, hasS = j > 0, hasN = j + 1 < ny;
+    const int iw = hasW ? i - 1 : i, ie = hasE ? i + 1 : i;
+    const int js = hasS ? j - 1 : j, jn = hasN ? j + 1 : j;
+#define AT(f, x, y) __ldg((f) + (size_t)(y) * pitch + (x))
+    const double up = AT(g.u, i, j), vp = AT(g.v, i, j), wp = AT(g.w, i, j);
+    // Table 1
+    const double hE = (1.0 - 0.5 * (up + AT(g.u, ie, j))) * (AT(g.v, ie, j) - vp);
+    const double hW = (1.0 - 0.5 * (up + AT(g.u, iw, j))) * (AT(g.v, iw, j) - vp);
+    const double hN = (1.0 - 0.5 * (up + AT(g.u, i, jn))) * (AT(g.v, i, jn) - vp);
+    const double hS = (1.0 - 0.5 * (up + AT(g.u, i, js))) * (AT(g.v, i, js) - vp);
+    const double d1 = (hE + hW) * k.ihx2 + (hN + hS) * k.ihy2;
+    // Table 2 in flux form
+    const double wE = AT(g.w, ie, j), wW = AT(g.w, iw, j), wN = AT(g.w, i, jn), wS = AT(g.w, i, js);
+    const double a11P = AT(g.a11, i, j), a22P = AT(g.a22, i, j), bP = AT(g.a12, i, j);
+    const double nE = (a11P + AT(g.a11, ie, j)) * (wE - wp);
+    const double nW = (AT(g.a11, iw, j) + a11P) * (wp - wW);
+    const double nN = (a22P + AT(g.a22, i, jn)) * (wN - wp);
+    const double nS = (AT(g.a22, i, js) + a22P) * (wp - wS);
+    const double tyP = wN - wS;
+    const double tyE = AT(g.w, ie, jn) - AT(g.w, ie, js);
+    const double tyW = AT(g.w, iw, jn) - AT(g.w, iw, js);
+    const double txP = wE - wW;
+    const double txN = AT(g.w, ie, jn) - AT(g.w, iw, jn);
+    const double txS = AT(g.w, ie, js) - AT(g.w, iw, js);
+    const double cE = hasE ? bP * tyP + AT(g.a12, ie, j) * tyE : 0.0;
+    const double cW = hasW ? AT(g.a12, iw, j) * tyW + bP * tyP : 0.0;
+    const double cN = hasN ? bP * txP + AT(g.a12, i, jn) * txN : 0.0;
+    const double cS = hasS ? AT(g.a12, i, js) * txS + bP * txP : 0.0;
+#undef AT
+    const double d2 = ((nE - nW) * k.kx + (nN - nS) * k.ky) + ((cE - cW) + (cN - cS)) * k.kc;
+    double fu, fv, fw;
+    if (k.no_reaction) {
+        fu = 0.0;
+        fv = k.D * d1;
+        fw = d2;
+    } else {
+        fu = up * (1.0 - up) - k.delta * up * wp;
+        fv = k.rho * vp * (1.0 - vp) + k.D * d1;
+        fw = k.c * (vp - wp) + d2;
+    }
+    const size_t o = (size_t)j * pitch + i;
+    g.uo[o] = up + k.dt * fu;
+    g.vo[o] = vp + k.dt * fv;
+    g.wo[o] = wp + k.dt * fw;
+}
+
+// ---------------------------------------------------------------- eq. (2)
+
+template <typename F>
+__global__ void coefficients_kernel(const double* __restrict__ theta, const double* __restrict__ l1,
+                                    const double* __restrict__ l2, int nx, int ny, F* a11, F* a12, F* a22,
+                                    int pitch, unsigned long long* counters, unsigned long long* lmax_bits)
+{
+    __shared__ double smax[32];
+    __shared__ unsigned long long sbad[32];
+    const size_t n = (size_t)nx * ny;
+    double lmax = 0.0;
+    unsigned long long bad = 0;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(q / nx), i = (int)(q % nx);
+        const double th = theta[q], L1 = l1[q], L2 = l2[q];
+        if (!(isfinite(th) && isfinite(L1) && isfinite(L2)) || !(L1 > 0.0) || !(L2 > 0.0)) ++bad;
+        double s, c;
+        sincos(th, &s, &c);
+        // A = R(theta) diag(L1, L2) R(theta)^T
+        const double A11 = L1 * c * c + L2 * s * s;
+        const double A12 = (L1 - L2) * s * c;
+        const double A22 = L1 * s * s + L2 * c * c;
+        const size_t o = (size_t)j * pitch + i;
+        a11[o] = (F)A11;
+        a12[o] = (F)A12;
+        a22[o] = (F)A22;
+        const double h = 0.5 * (A11 - A22);
+        const double e = 0.5 * (A11 + A22) + sqrt(h * h + A12 * A12);
+        if (e > lmax) lmax = e;  // NaN never wins
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, off));
+        bad += __shfl_xor_sync(0xffffffffu, bad, off);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        smax[wid] = lmax;
+        sbad[wid] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        unsigned long long b = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            m = fmax(m, smax[w]);
+            b += sbad[w];
+        }
+        if (b) atomicAdd(&counters[0], b);
+        atomicMax(lmax_bits, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// ---------------------------------------------------------------- layout conversion
+
+template <typename S, typename D>
+__global__ void unpack_kernel(const S* __restrict__ src, D* dst, int nx, int ny, int pitch,
+                              unsigned long long* nonfinite)
+{
+    const size_t n = (size_t)nx * ny;
+    unsigned long long bad = 0;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(q / nx), i = (int)(q % nx);
+        const S v = src[q];
+        if (!isfinite((double)v)) ++bad;
+        dst[(size_t)j * pitch + i] = (D)v;
+    }
+    if (nonfinite) {
+        for (int off = 16; off > 0; off >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, off);
+        if ((threadIdx.x & 31) == 0 && bad) atomicAdd(nonfinite, bad);
+    }
+}
+
+template <typename S, typename D>
+__global__ void pack_kernel(const S* __restrict__ src, D* dst, int nx, int ny, int pitch)
+{
+    const size_t n = (size_t)nx * ny;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(q / nx), i = (int)(q % nx);
+        dst[q] = (D)src[(size_t)j * pitch + i];
+    }
+}
+
+int blocks_for(size_t n, int threads) { return (int)std::min<size_t>((n + threads - 1) / threads, 152 * 16); }
+
+// ---------------------------------------------------------------- diagnostics
+
+struct DiagAcc {
+    double sum[3], mn[3], mx[3];
+    double nonfinite, tumour, gap;
+};
+
+__device__ __forceinline__ void diag_merge(DiagAcc& a, const DiagAcc& b)
+{
+    for (int f = 0; f < 3; ++f) {
+        a.sum[f] += b.sum[f];
+        a.mn[f] = fmin(a.mn[f], b.mn[f]);
+        a.mx[f] = fmax(a.mx[f], b.mx[f]);
+    }
+    a.nonfinite += b.nonfinite;
+    a.tumour += b.tumour;
+    a.gap += b.gap;
+}
+
+__device__ __forceinline__ DiagAcc diag_shfl(const DiagAcc& a, int off)
+{
+    DiagAcc b;
+    for (int f = 0; f < 3; ++f) {
+        b.sum[f] = __shfl_xor_sync(0xffffffffu, a.sum[f], off);
+        b.mn[f] = __shfl_xor_sync(0xffffffffu, a.mn[f], off);
+        b.mx[f] = __shfl_xor_sync(0xffffffffu, a.mx[f], off);
+    }
+    b.nonfinite = __shfl_xor_sync(0xffffffffu, a.nonfinite, off);
+    b.tumour = __shfl_xor_sync(0xffffffffu, a.tumour, off);
+    b.gap = __shfl_xor_sync(0xffffffffu, a.gap, off);
+    return b;
+}
+
+// Warp-shuffle then shared-memory block reduction; the result is valid in
+// thread 0.  The combination order is fixed, so the result is deterministic.
+__device__ DiagAcc diag_block_reduce(DiagAcc a)
+{
+    __shared__ DiagAcc sh[32];
+    for (int off = 16; off > 0; off >>= 1) diag_merge(a, diag_shfl(a, off));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) diag_merge(a, sh[w]);
+    }
+    return a;
+}
+
+__device__ __forceinline__ void diag_init(DiagAcc& a)
+{
+    for (int f = 0; f < 3; ++f) {
+        a.sum[f] = 0.0;
+        a.mn[f] = INFINITY;
+        a.mx[f] = -INFINITY;
+    }
+    a.nonfinite = a.tumour = a.gap = 0.0;
+}
+
+template <typename F>
+__global__ void __launch_bounds__(256) diag_partial_kernel(const F* __restrict__ u, const F* __restrict__ v,
+                                                           const F* __restrict__ w, int nx, int ny, int pitch,
+                                                           double eps, double* partials)
+{
+    DiagAcc a;
+    diag_init(a);
+    // Rows are distributed over blocks, columns over threads (coalesced).
+    for (int j = blockIdx.x; j < ny; j += gridDim.x) {
+        const size_t row = (size_t)j * pitch;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const double x[3] = {(double)u[row + i], (double)v[row + i], (double)w[row + i]};
+            for (int f = 0; f < 3; ++f) {
+                if (isfinite(x[f])) {
+                    a.sum[f] += x[f];
+                    a.mn[f] = fmin(a.mn[f], x[f]);
+                    a.mx[f] = fmax(a.mx[f], x[f]);
+                } else {
+                    a.nonfinite += 1.0;
+                }
+            }
+            if (x[1] > 0.5) a.tumour += 1.0;
+            if (x[0] < eps && x[1] < eps) a.gap += 1.0;
+        }
+    }
+    a = diag_block_reduce(a);
+    if (threadIdx.x == 0) {
+        double* p = partials + (size_t)blockIdx.x * kDiagStride;
+        for (int f = 0; f < 3; ++f) {
+            p[f] = a.sum[f];
+            p[3 + f] = a.mn[f];
+            p[6 + f] = a.mx[f];
+        }
+        p[9] = a.nonfinite;
+        p[10] = a.tumour;
+        p[11] = a.gap;
+    }
+}
+
+__global__ void __launch_bounds__(256) diag_final_kernel(const double* __restrict__ partials, int nparts,
+                                                         double* out)
+{
+    DiagAcc a;
+    diag_init(a);
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+        const double* p = partials + (size_t)b * kDiagStride;
+        DiagAcc c;
+        for (int f = 0; f < 3; ++f) {
+            c.sum[f] = p[f];
+            c.mn[f] = p[3 + f];
+            c.mx[f] = p[6 + f];
+        }
+        c.nonfinite = p[9];
+        c.tumour = p[10];
+        c.gap = p[11];
+        diag_merge(a, c);
+    }
+    a = diag_block_reduce(a);
+    if (threadIdx.x == 0) {
+        for (int f = 0; f < 3; ++f) {
+            out[f] = a.sum[f];
+            out[3 + f] = a.mn[f];
+            out[6 + f] = a.mx[f];
+        }
+        out[9] = a.nonfinite;
+        out[10] = a.tumour;
+        out[11] = a.gap;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_step64(const Grid64& g, const Rates64& r, cudaStream_t s)
+{
+    const dim3 block(32, 8);
+    const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8);
+    step64_kernel<<<grid, block, 0, s>>>(g, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coefficients(const double* theta, const double* l1, const double* l2, int nx, int ny, void* a11,
+                                void* a12, void* a22, int pitch, bool fp64, unsigned long long* counters,
+                                unsigned long long* lmax_bits, cudaStream_t s)
+{
+    const size_t n = (size_t)nx * ny;
+    const int blocks = blocks_for(n, 256);
+    if (fp64)
+        coefficients_kernel<double><<<blocks, 256, 0, s>>>(theta, l1, l2, nx, ny, (double*)a11, (double*)a12,
+                                                           (double*)a22, pitch, counters, lmax_bits);
+    else
+        coefficients_kernel<float><<<blocks, 256, 0, s>>>(theta, l1, l2, nx, ny, (float*)a11, (float*)a12,
+                                                          (float*)a22, pitch, counters, lmax_bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const void* src, bool src_fp64, void* dst, bool dst_fp64, int nx, int ny, int pitch,
+                          unsigned long long* nonfinite, cudaStream_t s)
+{
+    const size_t n = (size_t)nx * ny;
+    const int blocks = blocks_for(n, 256);
+    if (src_fp64 && dst_fp64)
+        unpack_kernel<double, double><<<blocks, 256, 0, s>>>((const double*)src, (double*)dst, nx, ny, pitch, nonfinite);
+    else if (src_fp64)
+        unpack_kernel<double, float><<<blocks, 256, 0, s>>>((const double*)src, (float*)dst, nx, ny, pitch, nonfinite);
+    else if (dst_fp64)
+        unpack_kernel<float, double><<<blocks, 256, 0, s>>>((const float*)src, (double*)dst, nx, ny, pitch, nonfinite);
+    else
+        unpack_kernel<float, float><<<blocks, 256, 0, s>>>((const float*)src, (float*)dst, nx, ny, pitch, nonfinite);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const void* src, bool src_fp64, void* dst, bool dst_fp64, int nx, int ny, int pitch,
+                        cudaStream_t s)
+{
+    const size_t n = (size_t)nx * ny;
+    const int blocks = blocks_for(n, 256);
+    if (src_fp64 && dst_fp64)
+        pack_kernel<double, double><<<blocks, 256, 0, s>>>((const double*)src, (double*)dst, nx, ny, pitch);
+    else if (src_fp64)
+        pack_kernel<double, float><<<blocks, 256, 0, s>>>((const double*)src, (float*)dst, nx, ny, pitch);
+    else if (dst_fp64)
+        pack_kernel<float, double><<<blocks, 256, 0, s>>>((const float*)src, (double*)dst, nx, ny, pitch);
+    else
+        pack_kernel<float, float><<<blocks, 256, 0, s>>>((const float*)src, (float*)dst, nx, ny, pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(const void* u, const void* v, const void* w, bool fp64, int nx, int ny, int pitch,
+                               double eps, double* partials, double* out, cudaStream_t s)
+{
+    const int blocks = std::min(ny, kDiagBlocks);
+    if (fp64)
+        diag_partial_kernel<double><<<blocks, 256, 0, s>>>((const double*)u, (const double*)v, (const double*)w, nx,
+                                                           ny, pitch, eps, partials);
+    else
+        diag_partial_kernel<float><<<blocks, 256, 0, s>>>((const float*)u, (const float*)v, (const float*)w, nx, ny,
+                                                          pitch, eps, partials);
+    diag_final_kernel<<<1, 256, 0, s>>>(partials, blocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace gg
