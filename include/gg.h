@@ -174,6 +174,32 @@ int gg_adjoint(gg_sim* sim, int64_t nsteps,
                float* g_u0, float* g_v0, float* g_w0,
                double* g_scalars, int64_t checkpoint_every);
 
+/* Diagnostics without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code
+ * running while its stream is captured into a CUDA graph, code inside a
+ * framework whose memory pool owns the device and forbids allocations it
+ * does not track, or a time-critical loop that cannot pay for the implicit
+ * synchronisation of cudaMalloc/cudaFree.  It computes exactly what
+ * gg_diagnostics_eps computes, from fields the caller already holds:
+ *   u, v, w: device, ny rows of `pitch` elements (float, or double when
+ *     fp64 != 0), row j starting at element j*pitch, nx <= pitch values used;
+ *   dx, dy > 0: cell sizes; eps > 0: gap threshold; *out: host result.
+ * Its scratch (608 partial records + 1 result record of 16 doubles, 77,952
+ * bytes) is a fixed array in the library's device memory, present on every
+ * device that loads the library until the process exits.  Limits: nx, ny >= 1,
+ * pitch >= nx and nx*ny <= 2^31 cells; anything else returns GG_ERR_ARG
+ * before any device work.  The first call on a device looks up the device
+ * address of the scratch array (one cudaGetSymbolAddress, no allocation);
+ * make that first call before any stream capture on that device.  All calls
+ * share the one array, and every record a call reads is written by that same
+ * call, so nothing needs clearing between calls; calls whose work overlaps on
+ * the GPU (other streams, other host threads) race on the array and must be
+ * serialised by the caller.  Returns GG_OK, GG_ERR_NONFINITE (with *out
+ * filled), GG_ERR_ARG or GG_ERR_CUDA.  Synchronizes cuda_stream. */
+int gg_diagnostics_noalloc(const void* u, const void* v, const void* w, int32_t fp64,
+                           int32_t nx, int32_t ny, int32_t pitch, double dx, double dy,
+                           double eps, void* cuda_stream, gg_diag* out);
+
 double gg_dt(const gg_sim* sim);              /* fixed dt (0 if sim is NULL) */
 double gg_dt_max(const gg_sim* sim);          /* stable bound dt_max */
 int64_t gg_step_count(const gg_sim* sim);     /* steps taken so far */

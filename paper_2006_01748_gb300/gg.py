@@ -76,6 +76,8 @@ _SIGNATURES = {
     "gg_write": (ctypes.c_int, [_VP, _I32, _VP, _I32, _I32]),
     "gg_diagnostics": (ctypes.c_int, [_VP, ctypes.POINTER(gg_diag)]),
     "gg_diagnostics_eps": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.POINTER(gg_diag)]),
+    "gg_diagnostics_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _I32, _I32, _I32, _I32, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double, _VP, ctypes.POINTER(gg_diag)]),
     "gg_adjoint": (ctypes.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _DP, _I64]),
     "gg_dt": (ctypes.c_double, [_VP]),
     "gg_dt_max": (ctypes.c_double, [_VP]),
