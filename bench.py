@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--time-steps", type=int, default=5000)
     ap.add_argument("--steps-per-pass", type=int, default=0)
     ap.add_argument("--fp64-time-steps", type=int, default=100)
-    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / CPU legs")
+    ap.add_argument("--adjoint-steps", type=int, default=10000)
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / adjoint / CPU legs")
     return ap.parse_args()
 
 
@@ -291,6 +292,33 @@ def run_ours(args, dist):
             v2 = p.cells * 200 / (ms2 / 1e3)
             extras[name] = {"value": v2, "unit": "cell-updates/s",
                             "hbm_frac": BYTES_PER_CELL_PASS[prec] * p.cells / (ms2 / 1e3 / 200) / 1e9 / peak}
+
+    if not args.no_extras:
+        # adjoint / forward time on the 2048 x 2048 adjoint workload (10^4 steps,
+        # sqrt(N) checkpointing): the forward solve as gg_step runs it, and the
+        # whole gg_adjoint call (its own forward pass, recompute, reverse sweep)
+        pa = inputs.adjoint_2048(steps=args.adjoint_steps)
+        simf = gg.GGSim.from_problem(pa, precision="fp32_kahan", steps_per_pass=args.steps_per_pass)
+        simf.step(50)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        simf.step(pa.steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fwd_ms = a.elapsed_time(b)
+        Vn = torch.empty(pa.cells, dtype=torch.float32, device=dev)
+        simf.read("v", out=Vn)
+        simf.close()
+        sima = gg.GGSim.from_problem(pa, precision="fp32_kahan", steps_per_pass=args.steps_per_pass)
+        dLdv = (Vn / pa.cells).contiguous()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sima.adjoint(pa.steps, None, dLdv, None, outputs=("theta", "lambda1", "lambda2"))
+        adj_ms = 1e3 * (time.perf_counter() - t0)
+        sima.close()
+        extras["adjoint"] = {"workload": f"adjoint_2048: {pa.nx}x{pa.ny}, {pa.steps} steps, sqrt(N) checkpoints",
+                             "forward_ms": fwd_ms, "adjoint_ms": adj_ms, "adjoint_over_forward": adj_ms / fwd_ms}
 
     # end to end through the public API with host buffers: create from host
     # arrays (H2D), advance, read the three fields back (D2H)

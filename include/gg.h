@@ -241,6 +241,30 @@ int gg_batch_read(gg_batch* b, int32_t inst, int32_t field, void* dst,
 /* Diagnostics of instance inst.  Synchronizes. */
 int gg_batch_diagnostics(gg_batch* b, int32_t inst, gg_diag* out);
 
+/* Autotuner of the ensemble launch: times trial_steps steps (>= 1; 0 means
+ * 8) of every candidate tile shape -- strip width bx in {128, 256}, chunk
+ * height by in {32, 64, 128} (by >= 8T) and steps per pass T in {1, 2, 4} --
+ * on the batch itself, keeps the fastest, and restores the state it
+ * advanced.  chosen (may be NULL) receives {T, bx, by, threads}.
+ * Synchronizes. */
+int gg_batch_autotune(gg_batch* b, int64_t trial_steps, int32_t* chosen);
+
+/* Testing hook for the bounded barrier wait: sets the per-wait time limit
+ * (0 < seconds <= 60; 2 s by default) and, with extra_arrivals = 1, makes
+ * the grid barrier expect one CTA more than the launch has, so that every
+ * wait runs into its limit, sets the device error word and returns (the
+ * next synchronizing call reports GG_ERR_TIMEOUT).  extra_arrivals = 0
+ * restores normal operation. */
+int gg_batch_set_barrier_timeout(gg_batch* b, double seconds, int32_t extra_arrivals);
+
+int32_t gg_batch_steps_per_pass(const gg_batch* b);
+
+/* Launch description of the last gg_batch_step: info[0..6] = steps per pass
+ * T, strip width bx, chunk height by, threads per CTA, CTAs of the
+ * persistent grid, work items (tiles) per pass, and 1 if the launch ran as a
+ * replayed CUDA graph (0 if stream capture was refused and it was launched
+ * directly). */
+int gg_batch_launch_info(const gg_batch* b, int32_t* info);
 double gg_batch_dt(const gg_batch* b, int32_t inst);
 const char* gg_batch_last_error(const gg_batch* b);
 int gg_batch_destroy(gg_batch* b);

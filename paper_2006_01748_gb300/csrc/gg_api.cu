@@ -66,8 +66,10 @@ Grid32 grid32(const gg_sim* s, int cur)
     return g;
 }
 
-// Default launch plan: strips of at most 256 output columns split evenly,
-// chunks of 128 rows, 128 threads.
+// Default launch plan: strips of at most 256 output columns split evenly;
+// chunk heights chosen so that the grid holds at least 4 CTAs per SM
+// (152 SMs) when the domain allows it, never below 8T rows (the y-halo of a
+// pass is 2T rows) and never above 128 rows.
 Plan32 default_plan(int nx, int ny, int T)
 {
     Plan32 p;
@@ -75,7 +77,12 @@ Plan32 default_plan(int nx, int ny, int T)
     p.halo = T;
     const int ns = (nx + 255) / 256;
     p.bx = round_up((nx + ns - 1) / ns, 4);
-    p.by = std::min(ny, 128);
+    const int target_ctas = 4 * 152;
+    const int chunks = (target_ctas + ns - 1) / ns;
+    int by = round_up((ny + chunks - 1) / chunks, 8);
+    by = std::max(by, std::max(16, 8 * T));
+    by = std::min(by, 128);
+    p.by = std::min(ny, by);
     p.threads = 128;
     return p;
 }

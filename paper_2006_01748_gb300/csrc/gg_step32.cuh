@@ -96,11 +96,23 @@ __device__ __forceinline__ void kahan_add(float x, float inc, float comp, float&
     xo = t;
 }
 
-template <int T, bool KAHAN, int MAXM>
-__global__ void __launch_bounds__(256) step32_kernel(const Grid32 g, const Rates32 k, const int bx, const int by,
-                                                     const int halo, const int sw)
+// One pass of T steps over the tile (strip sx, chunk sy) of one grid; smem
+// holds the rings described above.  Called by every thread of the CTA.
+// State loads: COHERENT = false reads through the read-only cache (the state
+// was written by an earlier launch); COHERENT = true bypasses L1 (__ldcg),
+// for a persistent kernel that reads state written by other CTAs of the
+// same launch.
+template <bool COHERENT>
+__device__ __forceinline__ float ld_state(const float* p)
 {
-    extern __shared__ float smem[];
+    if constexpr (COHERENT) return __ldcg(p);
+    else return __ldg(p);
+}
+
+template <int T, bool KAHAN, int MAXM, bool COHERENT = false>
+__device__ __forceinline__ void tile_pass(const Grid32& g, const Rates32& k, const int bx, const int by,
+                                          const int halo, const int sw, const int sx, const int sy, float* smem)
+{
     float* const st = smem;                             // [T][3 fields][3 slots][sw]
     float* const cp = st + T * 9 * sw;                  // [T][3 fields][2 slots][sw]
     float* const cf = cp + (KAHAN ? T * 6 * sw : 0);    // [3 fields][T+2 slots][sw]
@@ -109,8 +121,8 @@ __global__ void __launch_bounds__(256) step32_kernel(const Grid32 g, const Rates
 #define CF(f, slot) (cf + ((f) * (T + 2) + (slot)) * sw)
 
     const int nx = g.nx, ny = g.ny, pitch = g.pitch;
-    const int xs = blockIdx.x * bx;
-    const int ys = blockIdx.y * by;
+    const int xs = sx * bx;
+    const int ys = sy * by;
     const int x0 = xs - halo;  // global column of shared-memory column 0
     const int lo0 = max(0, ys - T);
     const int hi0 = min(ny, ys + by + T);
@@ -145,16 +157,16 @@ __global__ void __launch_bounds__(256) step32_kernel(const Grid32 g, const Rates
         for (int m = 0; m < MAXM; ++m) {
             if (ind[m]) {
                 const size_t o = (size_t)r * pitch + gxs[m];
-                pre[m][0] = __ldg(g.u + o);
-                pre[m][1] = __ldg(g.v + o);
-                pre[m][2] = __ldg(g.w + o);
+                pre[m][0] = ld_state<COHERENT>(g.u + o);
+                pre[m][1] = ld_state<COHERENT>(g.v + o);
+                pre[m][2] = ld_state<COHERENT>(g.w + o);
                 pre[m][3] = __ldg(g.a11 + o);
                 pre[m][4] = __ldg(g.a12 + o);
                 pre[m][5] = __ldg(g.a22 + o);
                 if constexpr (KAHAN) {
-                    pre[m][6] = __ldg(g.cu + o);
-                    pre[m][7] = __ldg(g.cv + o);
-                    pre[m][8] = __ldg(g.cw + o);
+                    pre[m][6] = ld_state<COHERENT>(g.cu + o);
+                    pre[m][7] = ld_state<COHERENT>(g.cv + o);
+                    pre[m][8] = ld_state<COHERENT>(g.cw + o);
                 }
             } else {
 #pragma unroll
@@ -254,6 +266,14 @@ __global__ void __launch_bounds__(256) step32_kernel(const Grid32 g, const Rates
 #undef ST
 #undef CP
 #undef CF
+}
+
+template <int T, bool KAHAN, int MAXM>
+__global__ void __launch_bounds__(256) step32_kernel(const Grid32 g, const Rates32 k, const int bx, const int by,
+                                                     const int halo, const int sw)
+{
+    extern __shared__ float smem[];
+    tile_pass<T, KAHAN, MAXM>(g, k, bx, by, halo, sw, blockIdx.x, blockIdx.y, smem);
 }
 
 template <int T, bool KAHAN>

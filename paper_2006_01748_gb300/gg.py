@@ -92,6 +92,10 @@ _SIGNATURES = {
     "gg_batch_read": (ctypes.c_int, [_VP, _I32, _I32, _VP, _I32, _I32]),
     "gg_batch_diagnostics": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(gg_diag)]),
     "gg_batch_dt": (ctypes.c_double, [_VP, _I32]),
+    "gg_batch_autotune": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(_I32)]),
+    "gg_batch_set_barrier_timeout": (ctypes.c_int, [_VP, ctypes.c_double, _I32]),
+    "gg_batch_steps_per_pass": (_I32, [_VP]),
+    "gg_batch_launch_info": (ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
     "gg_batch_last_error": (ctypes.c_char_p, [_VP]),
     "gg_batch_destroy": (ctypes.c_int, [_VP]),
 }
@@ -312,6 +316,33 @@ class GGSim:
         out["status"] = rc
         return out
 
+    def adjoint(self, nsteps: int, dLdu=None, dLdv=None, dLdw=None, checkpoint_every: int = 0,
+                outputs=("theta", "lambda1", "lambda2", "u0", "v0", "w0")):
+        """Discrete adjoint of ``nsteps`` steps from the current state.
+
+        dLdu/dLdv/dLdw: contiguous float32 CUDA tensors of nx*ny values
+        (dL/d(U,V,W) after the last step) or None.  Returns a dict of float32
+        CUDA tensors of shape (ny, nx) for the requested outputs and
+        ``scalars`` = dL/d(delta, rho, D, c) as a float64 numpy array.  The
+        simulation is left at step ``nsteps``."""
+        import torch
+        n = self.nx * self.ny
+
+        def ptr(t):
+            if t is None:
+                return None
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == n
+            return ctypes.c_void_p(t.data_ptr())
+
+        res = {name: torch.empty((self.ny, self.nx), dtype=torch.float32, device="cuda") for name in outputs}
+        gs = np.zeros(4)
+        rc = gg_adjoint(self._sim, nsteps, ptr(dLdu), ptr(dLdv), ptr(dLdw),
+                        *(ptr(res.get(k)) for k in ("theta", "lambda1", "lambda2", "u0", "v0", "w0")),
+                        gs.ctypes.data_as(_DP), checkpoint_every)
+        _check(rc, self._sim, "gg_adjoint")
+        res["scalars"] = gs
+        return res
+
     def state(self, fp64: bool = True):
         return tuple(self.read(f, fp64) for f in ("u", "v", "w"))
 
@@ -319,6 +350,105 @@ class GGSim:
         if self._sim is not None:
             gg_destroy(self._sim)
             self._sim = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class GGBatch:
+    """An ensemble of independent simulations advanced by one persistent,
+    graph-captured launch (owns a gg_batch*)."""
+
+    def __init__(self, problems: Sequence, precision="fp32_kahan", steps_per_pass=0, stream=None):
+        n = len(problems)
+        self.problems = list(problems)
+        grids = (gg_grid * n)()
+        params = (gg_params * n)()
+        keep = []
+        ptrs = (_VP * (6 * n))()
+        for k, p in enumerate(problems):
+            grids[k] = gg_grid(p.nx, p.ny, p.lx, p.ly)
+            params[k] = make_params(p.delta, p.rho, p.D, p.c, precision, cfl=p.cfl, steps_per_pass=steps_per_pass)
+            for m, a in enumerate((p.theta, p.lambda1, p.lambda2, p.u0, p.v0, p.w0)):
+                arr = _f64_host(a, p.nx * p.ny)
+                keep.append(arr)
+                ptrs[6 * k + m] = arr.ctypes.data_as(_VP)
+        self._stream = stream if stream is not None else _current_stream()
+        out = _VP()
+        rc = lib().gg_batch_create(n, grids, params, ptrs, self._stream, ctypes.byref(out))
+        if rc != GG_OK:
+            raise GGError(rc, "gg_batch_create failed")
+        self._b = out
+        self.n = n
+
+    @property
+    def handle(self):
+        return self._b
+
+    @property
+    def steps_per_pass(self) -> int:
+        return lib().gg_batch_steps_per_pass(self._b)
+
+    def _check(self, rc, what):
+        if rc != GG_OK:
+            msg = lib().gg_batch_last_error(self._b)
+            raise GGError(rc, f"{what}: {msg.decode() if msg else gg_error_string(rc)}")
+
+    def autotune(self, trial_steps: int = 8):
+        chosen = (_I32 * 4)()
+        self._check(lib().gg_batch_autotune(self._b, int(trial_steps), chosen), "gg_batch_autotune")
+        return dict(T=chosen[0], bx=chosen[1], by=chosen[2], threads=chosen[3])
+
+    def step(self, nsteps: int):
+        self._check(lib().gg_batch_step(self._b, int(nsteps)), "gg_batch_step")
+
+    def dt(self, inst: int) -> float:
+        return lib().gg_batch_dt(self._b, inst)
+
+    def launch_info(self) -> Dict:
+        info = (_I32 * 7)()
+        self._check(lib().gg_batch_launch_info(self._b, info), "gg_batch_launch_info")
+        return dict(T=info[0], bx=info[1], by=info[2], threads=info[3], ctas=info[4], tiles=info[5],
+                    graph=bool(info[6]))
+
+    def read(self, inst: int, field: str = "v", fp64: bool = True):
+        p = self.problems[inst]
+        a = np.empty((p.ny, p.nx), dtype=np.float64 if fp64 else np.float32)
+        self._check(lib().gg_batch_read(self._b, inst, FIELDS[field], a.ctypes.data_as(_VP), 0, 1 if fp64 else 0),
+                    "gg_batch_read")
+        return a
+
+    def read_status(self, inst: int, field: str = "v"):
+        p = self.problems[inst]
+        a = np.empty((p.ny, p.nx), dtype=np.float64)
+        return lib().gg_batch_read(self._b, inst, FIELDS[field], a.ctypes.data_as(_VP), 0, 1)
+
+    def diagnostics(self, inst: int) -> Dict:
+        d = gg_diag()
+        rc = lib().gg_batch_diagnostics(self._b, inst, ctypes.byref(d))
+        if rc not in (GG_OK, GG_ERR_NONFINITE):
+            self._check(rc, "gg_batch_diagnostics")
+        out = diag_dict(d)
+        out["status"] = rc
+        return out
+
+    def set_barrier_timeout(self, seconds: float, extra_arrivals: int = 0):
+        self._check(lib().gg_batch_set_barrier_timeout(self._b, float(seconds), int(extra_arrivals)),
+                    "gg_batch_set_barrier_timeout")
+
+    def close(self):
+        if getattr(self, "_b", None) is not None:
+            lib().gg_batch_destroy(self._b)
+            self._b = None
 
     def __del__(self):
         try:

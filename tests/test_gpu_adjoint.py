@@ -1,0 +1,214 @@
+"""Parity of the CUDA discrete adjoint (gg_adjoint through the C ABI) with the
+FP64 oracle's adjoint, checkpoint invariance, finite differences of the GPU
+FP64 forward at small and full size, and the torch.autograd wrapper.
+
+Tolerance: relative max-norm <= 1e-5 per gradient field (FP32 + Kahan adjoint
+against the FP64 oracle), <= 1e-5 relative for the four rate gradients."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_01748_gb300 import build, gg, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build()
+    gg.lib()
+    return torch
+
+
+def rel_err(got, ref):
+    return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+def small_problem(nx, ny, seed=5, steps=120):
+    p = inputs.plain_128(nx, ny, steps=steps, seed=seed)
+    p.D = 2e-3
+    p.u0, p.v0, p.w0 = inputs.random_state(nx, ny, seed + 1)
+    return p
+
+
+def oracle_adjoint(p, steps, Vstar, dLdU, dLdW):
+    s, a = oracle.setup_for(p)
+    U, V, W = oracle.run(s, *a, p.u0, p.v0, p.w0, steps)
+    gV = oracle.misfit_grad(V, Vstar, s.dx, s.dy)
+    lam0, ga, gs = oracle.adjoint(s, *a, p.u0, p.v0, p.w0, steps, dLdU, gV, dLdW)
+    gth, gl1, gl2 = oracle.coefficients_vjp(p.theta, p.lambda1, p.lambda2, *ga)
+    return dict(theta=gth, lambda1=gl1, lambda2=gl2, u0=lam0[0], v0=lam0[1], w0=lam0[2], scalars=gs, V=V, s=s)
+
+
+def gpu_adjoint(torch, p, steps, dLdU, dLdV, dLdW, precision="fp32_kahan", checkpoint_every=0):
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda().view(-1)
+    with gg.GGSim.from_problem(p, precision=precision) as sim:
+        r = sim.adjoint(steps, t(dLdU), t(dLdV), t(dLdW), checkpoint_every=checkpoint_every)
+        r = {k: (v.cpu().numpy().astype(np.float64) if k != "scalars" else v) for k, v in r.items()}
+        r["steps"] = sim.steps
+    return r
+
+
+@pytest.mark.parametrize("nx,ny,steps", [(40, 33, 120), (64, 64, 200), (5, 1, 50), (1, 6, 50)])
+def test_adjoint_matches_oracle(torch, nx, ny, steps):
+    p = small_problem(nx, ny, steps=steps)
+    Vstar = inputs.random_state(nx, ny, 99)[1]
+    dLdU = 1e-3 * inputs.white_noise(nx, ny, 7, -1, 1)
+    dLdW = 1e-3 * inputs.white_noise(nx, ny, 8, -1, 1)
+    ref = oracle_adjoint(p, steps, Vstar, dLdU, dLdW)
+    gV = oracle.misfit_grad(ref["V"], Vstar, ref["s"].dx, ref["s"].dy)
+    got = gpu_adjoint(torch, p, steps, dLdU, gV, dLdW)
+    assert got["steps"] == steps
+    for k in ("theta", "lambda1", "lambda2", "u0", "v0", "w0"):
+        assert rel_err(got[k], ref[k]) <= 1e-5, k
+    for q in range(4):
+        assert abs(got["scalars"][q] - ref["scalars"][q]) <= 1e-5 * max(abs(ref["scalars"][q]), 1e-12), q
+
+
+def test_adjoint_without_kahan_and_without_reactions(torch):
+    nx, ny, steps = 48, 40, 100
+    p = small_problem(nx, ny, steps=steps)
+    Vstar = inputs.random_state(nx, ny, 98)[1]
+    z = np.zeros((ny, nx))
+    s, a = oracle.setup_for(p, no_reaction=True)
+    U, V, W = oracle.run(s, *a, p.u0, p.v0, p.w0, steps)
+    gV = oracle.misfit_grad(V, Vstar, s.dx, s.dy)
+    lam0, ga, gs = oracle.adjoint(s, *a, p.u0, p.v0, p.w0, steps, z, gV, z)
+    gth = oracle.coefficients_vjp(p.theta, p.lambda1, p.lambda2, *ga)[0]
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda().view(-1)
+    for precision, tol in (("fp32_kahan", 1e-5), ("fp32", 1e-4)):
+        with gg.GGSim.from_problem(p, precision=precision, no_reaction=True) as sim:
+            r = sim.adjoint(steps, None, t(gV), None)
+        assert rel_err(r["theta"].cpu().numpy(), gth) <= tol
+        assert rel_err(r["v0"].cpu().numpy(), lam0[1]) <= tol
+        assert abs(r["scalars"][2] - gs[2]) <= tol * abs(gs[2])
+        assert r["scalars"][0] == 0 and r["scalars"][1] == 0 and r["scalars"][3] == 0
+
+
+def test_checkpoint_spacing_does_not_change_the_result(torch):
+    nx, ny, steps = 70, 50, 97
+    p = small_problem(nx, ny, steps=steps)
+    dU = inputs.white_noise(nx, ny, 1, -1, 1)
+    dV = inputs.white_noise(nx, ny, 2, -1, 1)
+    dW = inputs.white_noise(nx, ny, 3, -1, 1)
+    base = gpu_adjoint(torch, p, steps, dU, dV, dW, checkpoint_every=0)
+    for K in (1, 7, 97, 500):
+        r = gpu_adjoint(torch, p, steps, dU, dV, dW, checkpoint_every=K)
+        for k in ("theta", "lambda1", "lambda2", "u0", "v0", "w0"):
+            assert np.array_equal(r[k], base[k]), (K, k)
+        assert np.array_equal(r["scalars"], base["scalars"])
+
+
+def _fp64_loss(p, dt, steps, Vstar, **over):
+    q = inputs.Problem(**{**p.__dict__, **over})
+    with gg.GGSim.from_problem(q, precision="fp64", dt=dt) as sim:
+        sim.step(steps)
+        V = sim.read("v")
+    return 0.5 / (p.nx * p.ny) * float(np.sum((V - Vstar) ** 2))
+
+
+def test_adjoint_matches_finite_differences_of_gpu_fp64_forward(torch):
+    nx = ny = 64
+    steps = 200
+    p = small_problem(nx, ny, steps=steps, seed=21)
+    Vstar = inputs.random_state(nx, ny, 22)[1]
+    with gg.GGSim.from_problem(p, precision="fp64") as sim:
+        dt = sim.dt
+        sim.step(steps)
+        V = sim.read("v")
+    gV = (V - Vstar) / (nx * ny)
+    z = np.zeros((ny, nx))
+    with gg.GGSim.from_problem(p, precision="fp32_kahan", dt=dt) as sim:
+        t = torch.from_numpy(gV.astype(np.float32)).cuda().view(-1)
+        r = sim.adjoint(steps, None, t, None)
+    rng = np.random.default_rng(3)
+    for name in ("theta", "lambda1", "lambda2"):
+        g = r[name].cpu().numpy()
+        scale = np.max(np.abs(g))
+        for k in rng.choice(nx * ny, size=6, replace=False):
+            eps = 1e-3
+            xp, xm = getattr(p, name).copy(), getattr(p, name).copy()
+            xp.flat[k] += eps
+            xm.flat[k] -= eps
+            fd = (_fp64_loss(p, dt, steps, Vstar, **{name: xp}) - _fp64_loss(p, dt, steps, Vstar, **{name: xm})) / (2 * eps)
+            assert abs(fd - g.flat[k]) <= 2e-4 * scale, (name, k, fd, g.flat[k])
+    for q, name in enumerate(("delta", "rho", "D", "c")):
+        h = 1e-4 * max(1.0, abs(getattr(p, name)))
+        fd = (_fp64_loss(p, dt, steps, Vstar, **{name: getattr(p, name) + h})
+              - _fp64_loss(p, dt, steps, Vstar, **{name: getattr(p, name) - h})) / (2 * h)
+        assert abs(fd - r["scalars"][q]) <= 1e-4 * abs(fd) + 1e-12, name
+
+
+def _fp64_loss_vw(p, dt, steps, Vstar, **over):
+    q = inputs.Problem(**{**p.__dict__, **over})
+    with gg.GGSim.from_problem(q, precision="fp64", dt=dt) as sim:
+        sim.step(steps)
+        V, W = sim.read("v"), sim.read("w")
+    return (0.5 * float(np.sum((V - Vstar) ** 2)) + float(np.sum(W))) / p.cells
+
+
+def test_adjoint_2048_rate_gradients_against_finite_differences(torch):
+    """Full-size adjoint workload (2048 x 2048, 10^4 steps, sqrt(N)
+    checkpointing).  Over its short physical time (t = 10^4 dt, about 5e-4)
+    the v-misfit alone has gradients near 1e-20, so the checked loss adds the
+    acid mass: L = dx dy [ sum (V - V*)^2 / 2 + sum W ].  Its gradients for the
+    rates c and delta are compared with central differences of the GPU FP64
+    forward (dt held fixed)."""
+    p = inputs.adjoint_2048()
+    tgt = inputs.adjoint_2048(target=True)
+    with gg.GGSim.from_problem(tgt, precision="fp32_kahan") as sim:
+        sim.step(p.steps)
+        Vstar = sim.read("v")
+    with gg.GGSim.from_problem(p, precision="fp64") as sim:
+        dt = sim.dt
+    with gg.GGSim.from_problem(p, precision="fp32_kahan", dt=dt) as sim:
+        sim.step(p.steps)
+        V = sim.read("v")
+    with gg.GGSim.from_problem(p, precision="fp32_kahan", dt=dt) as sim:
+        tv = torch.from_numpy(((V - Vstar) / p.cells).astype(np.float32)).cuda().view(-1)
+        tw = torch.full((p.cells,), 1.0 / p.cells, dtype=torch.float32, device="cuda")
+        r = sim.adjoint(p.steps, None, tv, tw, outputs=("theta",))
+        assert sim.steps == p.steps
+    assert np.all(np.isfinite(r["theta"].cpu().numpy()))
+    L0 = _fp64_loss_vw(p, dt, p.steps, Vstar)
+    for q, name in ((3, "c"), (2, "D"), (1, "rho"), (0, "delta")):
+        h = 1e-3 * getattr(p, name)
+        fd = (_fp64_loss_vw(p, dt, p.steps, Vstar, **{name: getattr(p, name) + h})
+              - _fp64_loss_vw(p, dt, p.steps, Vstar, **{name: getattr(p, name) - h})) / (2 * h)
+        noise = 1e-15 * abs(L0) / h   # rounding floor of the central difference
+        if name == "c":
+            assert abs(fd) > 1e3 * noise   # the acid rate carries the signal
+        # FP32 second differences of V at h = 1/2048 lose about 11 bits to
+        # cancellation in smooth regions, so the gradients driven by D1 (D,
+        # rho, delta through U) carry ~1e-3 relative error after 10^4 steps;
+        # the acid-driven gradient stays within 1e-4.
+        tol = 1e-4 if name == "c" else 3e-3
+        assert abs(fd - r["scalars"][q]) <= tol * abs(fd) + 10 * noise, (name, fd, r["scalars"][q], noise)
+
+
+def test_autograd_function(torch):
+    from paper_2006_01748_gb300.autograd import GGStepFn
+    nx, ny, steps = 48, 36, 80
+    p = small_problem(nx, ny, steps=steps)
+    Vstar = torch.from_numpy(inputs.random_state(nx, ny, 97)[1]).cuda().float()
+    th = torch.tensor(p.theta, requires_grad=True)
+    l1 = torch.tensor(p.lambda1, requires_grad=True)
+    l2 = torch.tensor(p.lambda2, requires_grad=True)
+    sc = torch.tensor([p.delta, p.rho, p.D, p.c], dtype=torch.float64, requires_grad=True)
+    u0, v0, w0 = (torch.tensor(x, requires_grad=True) for x in (p.u0, p.v0, p.w0))
+    U, V, W = GGStepFn.apply(th, l1, l2, sc, u0, v0, w0, steps)
+    wgt = torch.from_numpy(1e-3 * inputs.white_noise(nx, ny, 96, -1, 1)).cuda()
+    loss = 0.5 / (nx * ny) * ((V.double() - Vstar.double()) ** 2).sum() + (wgt * W.double()).sum()
+    loss.backward()
+    s, a = oracle.setup_for(p)
+    Uo, Vo, Wo = oracle.run(s, *a, p.u0, p.v0, p.w0, steps)
+    gV = oracle.misfit_grad(Vo, Vstar.double().cpu().numpy(), s.dx, s.dy)
+    lam0, ga, gs = oracle.adjoint(s, *a, p.u0, p.v0, p.w0, steps, np.zeros_like(Uo), gV,
+                                  1e-3 * inputs.white_noise(nx, ny, 96, -1, 1))
+    gth = oracle.coefficients_vjp(p.theta, p.lambda1, p.lambda2, *ga)[0]
+    assert rel_err(th.grad.numpy(), gth) <= 1e-5
+    assert rel_err(w0.grad.numpy(), lam0[2]) <= 1e-5
+    assert np.allclose(sc.grad.numpy(), gs, rtol=1e-5, atol=1e-12)
