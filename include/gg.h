@@ -200,6 +200,24 @@ int gg_diagnostics_noalloc(const void* u, const void* v, const void* w, int32_t 
                            int32_t nx, int32_t ny, int32_t pitch, double dx, double dy,
                            double eps, void* cuda_stream, gg_diag* out);
 
+/* Autotuner of the FP32 step: times trial_steps steps (0 means 24) of every
+ * candidate launch plan -- the warp-register wavefront with T = 1..4 steps
+ * per pass and chunk heights 16..256 rows, the shared-memory wavefront with
+ * T in {1, 2, 4, 8} -- on this simulation, keeps the fastest and restores the
+ * state it advanced (every plan computes the same bits).  gg_create runs it
+ * by itself, once per (nx, ny, precision) and process, when
+ * steps_per_pass == 0 and nx*ny >= 2^18.  chosen (may be NULL) receives
+ * {T, kernel kind (1 warp, 0 shared memory), strip width, chunk height}.
+ * A no-op for GG_FP64_PLAIN.  Synchronizes. */
+int gg_autotune(gg_sim* sim, int64_t trial_steps, int32_t* chosen);
+
+/* Choose the launch plan of the FP32 step explicitly: kind 1 = warp-register
+ * wavefront (T = 1..4), kind 0 = shared-memory wavefront (T = 1..8);
+ * strip = output columns per CTA strip (kind 0 only, 0 = default), chunk =
+ * rows per chunk (0 = default).  Every plan computes the same bits.
+ * GG_ERR_ARG for values out of range, GG_ERR_STATE for GG_FP64_PLAIN. */
+int gg_set_plan(gg_sim* sim, int32_t kind, int32_t T, int32_t strip, int32_t chunk);
+
 double gg_dt(const gg_sim* sim);              /* fixed dt (0 if sim is NULL) */
 double gg_dt_max(const gg_sim* sim);          /* stable bound dt_max */
 int64_t gg_step_count(const gg_sim* sim);     /* steps taken so far */

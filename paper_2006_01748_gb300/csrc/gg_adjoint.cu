@@ -353,7 +353,7 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
             g.cwo = kahan ? w->scomp[(kk + 1) & 1][2] : nullptr;
             g.a11 = s->a32[0]; g.a12 = s->a32[1]; g.a22 = s->a32[2];
             g.nx = s->nx; g.ny = s->ny; g.pitch = s->pitch;
-            e = launch_step32(g, r, plan1, 1, kahan, st);
+            e = launch_plan(g, r, plan1, 1, kahan, st);
         }
         for (int kk = len - 1; kk >= 0 && e == cudaSuccess; --kk) {
             AdjArgs a;

@@ -6,7 +6,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "gg_internal.cuh"
 #include "gg_sim.cuh"
@@ -66,15 +69,34 @@ Grid32 grid32(const gg_sim* s, int cur)
     return g;
 }
 
-// Default launch plan: strips of at most 256 output columns split evenly;
-// chunk heights chosen so that the grid holds at least 4 CTAs per SM
-// (152 SMs) when the domain allows it, never below 8T rows (the y-halo of a
-// pass is 2T rows) and never above 128 rows.
+// Default launch plan: the warp-register wavefront with chunks of rows sized
+// so that the grid holds about 16 warps per SM (152 SMs) when the domain
+// allows it, never below 4T + 8 rows and never above 256 rows.  For T > 4 the
+// shared-memory wavefront (strips of at most 256 columns, chunks of 8T..128
+// rows, about 4 CTAs per SM).
 Plan32 default_plan(int nx, int ny, int T)
 {
     Plan32 p;
     p.T = T;
     p.halo = T;
+    p.threads = 128;
+    if (T <= 4) {
+        // warp-register wavefront; chunk heights from the 8192 x 8192 sweep
+        // (64 rows for T <= 2, 128 for T = 3, 256 for T = 4), lowered when the
+        // grid would give fewer than about 16 warps per SM
+        p.kind = 1;
+        const int out = 32 - 2 * T;
+        const int nstrips = (nx + out - 1) / out;
+        const int preferred = T <= 2 ? 64 : (T == 3 ? 128 : 256);
+        const int target_warps = 16 * 152;
+        const int chunks = std::max(1, (target_warps + nstrips - 1) / nstrips);
+        int H = round_up((ny + chunks - 1) / chunks, 8);
+        H = std::max(std::min(H, preferred), 4 * T + 8);
+        p.by = std::min(ny, H);
+        p.bx = out;
+        return p;
+    }
+    p.kind = 0;
     const int ns = (nx + 255) / 256;
     p.bx = round_up((nx + ns - 1) / ns, 4);
     const int target_ctas = 4 * 152;
@@ -83,7 +105,114 @@ Plan32 default_plan(int nx, int ny, int T)
     by = std::max(by, std::max(16, 8 * T));
     by = std::min(by, 128);
     p.by = std::min(ny, by);
-    p.threads = 128;
+    return p;
+}
+
+// ---------------------------------------------------------------- autotuner
+//
+// Times every candidate plan on the simulation itself and keeps the fastest
+// per step: the warp-register wavefront with T in {1, 2, 3, 4} and chunk
+// heights {16, 32, 64, 128, 256}, and the shared-memory wavefront with T in
+// {1, 2, 4, 8} and chunk heights {32, 64, 128}.  The state it advances is
+// saved first and restored afterwards, so tuning leaves the run unchanged
+// (every plan computes the same bits).  Results are cached per process by
+// (nx, ny, precision).
+namespace {
+struct TuneKey {
+    int nx, ny, precision;
+    bool operator<(const TuneKey& o) const
+    {
+        return nx != o.nx ? nx < o.nx : ny != o.ny ? ny < o.ny : precision < o.precision;
+    }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, Plan32> g_tune_cache;
+}  // namespace
+
+Plan32 tune_plan(gg_sim* s, int64_t trial_steps)
+{
+    const bool kahan = s->params.precision == GG_FP32_KAHAN;
+    const int nstate = kahan ? 6 : 3;
+    if (trial_steps < 1) trial_steps = 24;
+    const int64_t n = (trial_steps + 23) / 24 * 24;  // a multiple of every T tried
+    std::vector<Plan32> cands;
+    for (int T = 1; T <= 4; ++T)
+        for (int H : {16, 32, 64, 128, 256}) {
+            if (H < 4 * T + 8 && H != 256) continue;
+            Plan32 p = default_plan(s->nx, s->ny, T);
+            p.kind = 1;
+            p.by = std::min(s->ny, H);
+            cands.push_back(p);
+        }
+    for (int T : {1, 2, 4, 8})
+        for (int by : {32, 64, 128}) {
+            if (by < 8 * T) continue;
+            Plan32 p = default_plan(s->nx, s->ny, 8);  // shared-memory geometry
+            p.T = T;
+            p.halo = T;
+            p.by = std::min(s->ny, by);
+            cands.push_back(p);
+        }
+    const size_t fbytes = (size_t)s->pitch * s->ny * 4;
+    void* save = nullptr;
+    Plan32 best = s->plan;
+    if (cudaMalloc(&save, fbytes * nstate) != cudaSuccess) {
+        cudaGetLastError();
+        return best;  // no room to tune: keep the default plan
+    }
+    cudaError_t e = cudaSuccess;
+    for (int f = 0; f < nstate && e == cudaSuccess; ++f)
+        e = cudaMemcpyAsync((char*)save + f * fbytes, s->f32[s->cur][f], fbytes, cudaMemcpyDeviceToDevice, s->stream);
+    const Rates32 r = rates32(s);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best_ms = 1e300;
+    int cur = s->cur;
+    for (const Plan32& p : cands) {
+        if (e != cudaSuccess) break;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // rep 0 warms up
+            if (rep == 1) e = cudaEventRecord(e0, s->stream);
+            for (int64_t k = 0; k < n && e == cudaSuccess; k += p.T) {
+                e = launch_plan(grid32(s, cur), r, p, p.T, kahan, s->stream);
+                cur ^= 1;
+            }
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = p;
+        }
+    }
+    // restore the state into the current buffer
+    for (int f = 0; f < nstate && e == cudaSuccess; ++f)
+        e = cudaMemcpyAsync(s->f32[s->cur][f], (char*)save + f * fbytes, fbytes, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(save);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        s->last_error = std::string("autotune: ") + cudaGetErrorString(e);
+        return s->plan;
+    }
+    return best;
+}
+
+Plan32 cached_plan(gg_sim* s)
+{
+    const TuneKey key{s->nx, s->ny, s->params.precision};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) return it->second;
+    }
+    const Plan32 p = tune_plan(s, 24);
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = p;
     return p;
 }
 
@@ -276,6 +405,12 @@ int gg_create(const gg_grid* grid, const gg_params* params, const double* theta,
     if (!fp64) {
         const int T = s->params.steps_per_pass > 0 ? s->params.steps_per_pass : 1;
         s->plan = default_plan(s->nx, s->ny, T);
+        // steps_per_pass == 0: tuned (grids below 2^18 cells keep the default,
+        // they finish in microseconds either way)
+        if (s->params.steps_per_pass == 0 && (int64_t)s->nx * s->ny >= (int64_t)1 << 18) {
+            s->plan = cached_plan(s);
+            s->last_error.clear();
+        }
     }
     *out = s;
     return GG_OK;
@@ -308,7 +443,7 @@ int gg_step(gg_sim* s, int64_t nsteps)
         int64_t left = nsteps;
         while (left > 0 && e == cudaSuccess) {
             const int T = (int)std::min<int64_t>(left, s->plan.T);
-            e = launch_step32(grid32(s, s->cur), r, s->plan, T, kahan, s->stream);
+            e = launch_plan(grid32(s, s->cur), r, s->plan, T, kahan, s->stream);
             if (e == cudaSuccess) { s->cur ^= 1; s->steps += T; left -= T; }
         }
     }
@@ -426,6 +561,42 @@ int gg_diagnostics_eps(gg_sim* s, double eps, gg_diag* out)
 }
 
 int gg_diagnostics(gg_sim* s, gg_diag* out) { return gg_diagnostics_eps(s, 0.01, out); }
+
+int gg_autotune(gg_sim* s, int64_t trial_steps, int32_t* chosen)
+{
+    if (!s) return GG_ERR_ARG;
+    if (s->params.precision == GG_FP64_PLAIN) {
+        if (chosen) { chosen[0] = 1; chosen[1] = 0; chosen[2] = 0; chosen[3] = 0; }
+        return GG_OK;
+    }
+    const Plan32 best = tune_plan(s, trial_steps);
+    if (!s->last_error.empty() && s->last_error.rfind("autotune", 0) == 0) return GG_ERR_CUDA;
+    s->plan = best;
+    if (chosen) { chosen[0] = best.T; chosen[1] = best.kind; chosen[2] = best.bx; chosen[3] = best.by; }
+    return GG_OK;
+}
+
+int gg_set_plan(gg_sim* s, int32_t kind, int32_t T, int32_t strip, int32_t chunk)
+{
+    if (!s) return GG_ERR_ARG;
+    if (s->params.precision == GG_FP64_PLAIN) { s->last_error = "FP64 has a single plan"; return GG_ERR_STATE; }
+    if (kind != 0 && kind != 1) { s->last_error = "kind must be 0 or 1"; return GG_ERR_ARG; }
+    if (T < 1 || T > (kind == 1 ? 4 : kMaxT)) { s->last_error = "T out of range for this kernel"; return GG_ERR_ARG; }
+    if (chunk < 0 || strip < 0 || chunk > (1 << 20) || strip > 1024) { s->last_error = "bad strip or chunk"; return GG_ERR_ARG; }
+    Plan32 p = default_plan(s->nx, s->ny, kind == 1 ? T : kMaxT);
+    p.kind = kind;
+    p.T = T;
+    p.halo = T;
+    if (kind == 0) {
+        if (strip > 0) p.bx = round_up(strip, 4);
+        const int sw = p.bx + 2 * p.halo;
+        if ((sw + p.threads - 1) / p.threads > 3) { s->last_error = "strip too wide"; return GG_ERR_ARG; }
+    }
+    if (chunk > 0) p.by = std::min(s->ny, chunk);
+    if (kind == 1 && chunk == 0) p.by = default_plan(s->nx, s->ny, T).by;
+    s->plan = p;
+    return GG_OK;
+}
 
 int gg_destroy(gg_sim* s)
 {

@@ -35,15 +35,20 @@ struct Rates32 {
     int no_reaction;
 };
 
-// Launch plan of the FP32 step kernel: strips of bx output columns (plus a
-// halo of `halo` columns on each side), chunks of by output rows, `threads`
-// threads per CTA, T steps per pass.
+// Launch plan of the FP32 step.  kind 0: shared-memory wavefront (strips of
+// bx output columns plus a halo of `halo` columns on each side, chunks of by
+// output rows, `threads` threads per CTA); kind 1: warp-register wavefront
+// (strips of 32 - 2T columns per warp, chunks of by rows).  T steps per pass.
 struct Plan32 {
+    int kind = 1;
     int T = 1;
     int bx = 256, by = 128, halo = 1, threads = 128;
 };
 
 size_t step32_smem_bytes(const Plan32& p, bool kahan);
+cudaError_t launch_stepw(const Grid32& g, const Rates32& r, int H, int T, bool kahan, cudaStream_t s);
+// One pass of T steps with the kernel the plan names.
+cudaError_t launch_plan(const Grid32& g, const Rates32& r, const Plan32& p, int T, bool kahan, cudaStream_t s);
 cudaError_t launch_step32(const Grid32& g, const Rates32& r, const Plan32& p, int T, bool kahan,
                           cudaStream_t s);
 

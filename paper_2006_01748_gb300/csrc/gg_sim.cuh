@@ -39,6 +39,7 @@ Rates32 rates32(const gg_sim* s);
 Grid32 grid32(const gg_sim* s, int cur);
 Plan32 default_plan(int nx, int ny, int T);
 double stable_dt_max(double dx, double dy, double Lambda, const gg_params& p);
+Plan32 tune_plan(gg_sim* s, int64_t trial_steps);
 }  // namespace gg
 
 // Frees workspaces owned by other translation units (adjoint).

@@ -21,6 +21,7 @@
 #pragma once
 
 #include "gg_internal.cuh"
+#include "gg_math.cuh"
 
 namespace gg {
 namespace step32 {
@@ -30,70 +31,33 @@ struct Rows {
     const float *a11P, *a12S, *a12P, *a12N, *a22S, *a22P, *a22N;
 };
 
-// Rates (fu, fv, fw) of eq. (3) at one cell.  lxW / lxE are the west / east
-// neighbours in shared memory, equal to lx at a domain boundary (mirror
-// ghost); the row pointers S / N are already mirrored in the same way.
-// mW, mE, mS, mN are kc (= 1/(4 dx dy)) for interior faces and 0 for
-// boundary faces.
-__device__ __forceinline__ void cell_rates(const Rows& R, const Rates32& k, int lx, int lxW, int lxE, float mW,
-                                           float mE, float mS, float mN, float& up, float& vp, float& wp,
+// Rates (fu, fv, fw) of eq. (3) at one cell from shared-memory rows.  lxW /
+// lxE are the west / east neighbours, equal to lx at a domain boundary
+// (mirror ghost); the row pointers S / N are mirrored in the same way.  The
+// four faces are computed with the shared face functions of gg_math.cuh,
+// each with its two cells in west-east / south-north order, and a boundary
+// face carries zero flux.
+__device__ __forceinline__ void cell_rates(const Rows& R, const Rates32& k, int lx, int lxW, int lxE, bool hasW,
+                                           bool hasE, bool hasS, bool hasN, float& up, float& vp, float& wp,
                                            float& fu, float& fv, float& fw)
 {
     up = R.uP[lx];
     vp = R.vP[lx];
     wp = R.wP[lx];
-    // Table 1: sum over faces of (1 - (U_P + U_nb)/2) (V_nb - V_P) / h^2.
-    const float uE = R.uP[lxE], uW = R.uP[lxW], uN = R.uN[lx], uS = R.uS[lx];
-    const float vE = R.vP[lxE], vW = R.vP[lxW], vN = R.vN[lx], vS = R.vS[lx];
-    const float hE = (1.0f - 0.5f * (up + uE)) * (vE - vp);
-    const float hW = (1.0f - 0.5f * (up + uW)) * (vW - vp);
-    const float hN = (1.0f - 0.5f * (up + uN)) * (vN - vp);
-    const float hS = (1.0f - 0.5f * (up + uS)) * (vS - vp);
-    const float d1 = (hE + hW) * k.ihx2 + (hN + hS) * k.ihy2;
-
-    // Table 2 as face fluxes: normal part (arithmetic-mean a11 / a22) ...
     const float wE = R.wP[lxE], wW = R.wP[lxW], wN = R.wN[lx], wS = R.wS[lx];
-    const float a11P = R.a11P[lx], a22P = R.a22P[lx];
-    const float nE = (a11P + R.a11P[lxE]) * (wE - wp);
-    const float nW = (R.a11P[lxW] + a11P) * (wp - wW);
-    const float nN = (a22P + R.a22N[lx]) * (wN - wp);
-    const float nS = (R.a22S[lx] + a22P) * (wp - wS);
-    // ... and cross part: a12 times the tangential central difference at the
-    // two cells of each face (mirror ghosts in the tangential direction).
-    const float bP = R.a12P[lx];
-    const float tyP = wN - wS;
-    const float tyE = R.wN[lxE] - R.wS[lxE];
-    const float tyW = R.wN[lxW] - R.wS[lxW];
-    const float txP = wE - wW;
-    const float txN = R.wN[lxE] - R.wN[lxW];
-    const float txS = R.wS[lxE] - R.wS[lxW];
-    const float cE = bP * tyP + R.a12P[lxE] * tyE;
-    const float cW = R.a12P[lxW] * tyW + bP * tyP;
-    const float cN = bP * txP + R.a12N[lx] * txN;
-    const float cS = R.a12S[lx] * txS + bP * txP;
-    const float d2 = ((nE - nW) * k.kx + (nN - nS) * k.ky) + ((mE * cE - mW * cW) + (mN * cN - mS * cS));
-
-    if (k.no_reaction) {
-        fu = 0.0f;
-        fv = k.D * d1;
-        fw = d2;
-    } else {
-        fu = up * (1.0f - up) - k.delta * up * wp;
-        fv = k.rho * vp * (1.0f - vp) + k.D * d1;
-        fw = k.c * (vp - wp) + d2;
-    }
-}
-
-// x' = x + dt f with the Kahan compensation comp (the negated low-order
-// part lost by the previous additions): y = dt f - comp, t = x + y,
-// comp' = (t - x) - y.  The additions use explicit round-to-nearest
-// intrinsics so that they are neither contracted nor reassociated.
-__device__ __forceinline__ void kahan_add(float x, float inc, float comp, float& xo, float& compo)
-{
-    const float y = __fsub_rn(inc, comp);
-    const float t = __fadd_rn(x, y);
-    compo = __fsub_rn(__fsub_rn(t, x), y);
-    xo = t;
+    const float wNE = R.wN[lxE], wNW = R.wN[lxW], wSE = R.wS[lxE], wSW = R.wS[lxW];
+    const float tyP = __fsub_rn(wN, wS), tyE = __fsub_rn(wNE, wSE), tyW = __fsub_rn(wNW, wSW);
+    const float txP = __fsub_rn(wE, wW), txN = __fsub_rn(wNE, wNW), txS = __fsub_rn(wSE, wSW);
+    const float a11P = R.a11P[lx], bP = R.a12P[lx], a22P = R.a22P[lx];
+    const float gE = hasE ? fvm::gx_face(k, a11P, R.a11P[lxE], wp, wE, bP, tyP, R.a12P[lxE], tyE) : 0.0f;
+    const float gW = hasW ? fvm::gx_face(k, R.a11P[lxW], a11P, wW, wp, R.a12P[lxW], tyW, bP, tyP) : 0.0f;
+    const float gN = hasN ? fvm::gy_face(k, a22P, R.a22N[lx], wp, wN, bP, txP, R.a12N[lx], txN) : 0.0f;
+    const float gS = hasS ? fvm::gy_face(k, R.a22S[lx], a22P, wS, wp, R.a12S[lx], txS, bP, txP) : 0.0f;
+    const float hE = hasE ? fvm::h_face(up, R.uP[lxE], vp, R.vP[lxE], k.ihx2) : 0.0f;
+    const float hW = hasW ? fvm::h_face(R.uP[lxW], up, R.vP[lxW], vp, k.ihx2) : 0.0f;
+    const float hN = hasN ? fvm::h_face(up, R.uN[lx], vp, R.vN[lx], k.ihy2) : 0.0f;
+    const float hS = hasS ? fvm::h_face(R.uS[lx], up, R.vS[lx], vp, k.ihy2) : 0.0f;
+    fvm::rates_faces(k, up, vp, wp, hE, hW, hN, hS, gE, gW, gN, gS, fu, fv, fw);
 }
 
 // One pass of T steps over the tile (strip sx, chunk sy) of one grid; smem
@@ -131,7 +95,7 @@ __device__ __forceinline__ void tile_pass(const Grid32& g, const Rates32& k, con
 
     // Columns owned by this thread.
     int lxs[MAXM], lxw[MAXM], lxe[MAXM], gxs[MAXM];
-    float mWs[MAXM], mEs[MAXM];
+    bool hWs[MAXM], hEs[MAXM];
     bool act[MAXM], ind[MAXM], outc[MAXM];
 #pragma unroll
     for (int m = 0; m < MAXM; ++m) {
@@ -144,8 +108,8 @@ __device__ __forceinline__ void tile_pass(const Grid32& g, const Rates32& k, con
         const bool hasW = gx > 0, hasE = gx + 1 < nx;
         lxw[m] = hasW ? max(lx - 1, 0) : lx;
         lxe[m] = hasE ? min(lx + 1, sw - 1) : lx;
-        mWs[m] = hasW ? k.kc : 0.0f;
-        mEs[m] = hasE ? k.kc : 0.0f;
+        hWs[m] = hasW;
+        hEs[m] = hasE;
         outc[m] = ind[m] && lx >= halo && lx < halo + bx;
     }
 
@@ -218,7 +182,6 @@ __device__ __forceinline__ void tile_pass(const Grid32& g, const Rates32& k, con
                 R.a11P = CF(0, cPs);
                 R.a12S = CF(1, cS); R.a12P = CF(1, cPs); R.a12N = CF(1, cN);
                 R.a22S = CF(2, cS); R.a22P = CF(2, cPs); R.a22N = CF(2, cN);
-                const float mS = hasS ? k.kc : 0.0f, mN = hasN ? k.kc : 0.0f;
                 const int s2 = r % 2;
 #pragma unroll
                 for (int m = 0; m < MAXM; ++m) {
@@ -226,16 +189,16 @@ __device__ __forceinline__ void tile_pass(const Grid32& g, const Rates32& k, con
                     if (t == T && !outc[m]) continue;
                     const int lx = lxs[m];
                     float up, vp, wp, fu, fv, fw;
-                    cell_rates(R, k, lx, lxw[m], lxe[m], mWs[m], mEs[m], mS, mN, up, vp, wp, fu, fv, fw);
+                    cell_rates(R, k, lx, lxw[m], lxe[m], hWs[m], hEs[m], hasS, hasN, up, vp, wp, fu, fv, fw);
                     float un, vn, wn, cun = 0.f, cvn = 0.f, cwn = 0.f;
                     if constexpr (KAHAN) {
-                        kahan_add(up, k.dt * fu, CP(t - 1, 0, s2)[lx], un, cun);
-                        kahan_add(vp, k.dt * fv, CP(t - 1, 1, s2)[lx], vn, cvn);
-                        kahan_add(wp, k.dt * fw, CP(t - 1, 2, s2)[lx], wn, cwn);
+                        fvm::kahan_step(up, k.dt, fu, CP(t - 1, 0, s2)[lx], un, cun);
+                        fvm::kahan_step(vp, k.dt, fv, CP(t - 1, 1, s2)[lx], vn, cvn);
+                        fvm::kahan_step(wp, k.dt, fw, CP(t - 1, 2, s2)[lx], wn, cwn);
                     } else {
-                        un = up + k.dt * fu;
-                        vn = vp + k.dt * fv;
-                        wn = wp + k.dt * fw;
+                        un = fvm::euler_step(up, k.dt, fu);
+                        vn = fvm::euler_step(vp, k.dt, fv);
+                        wn = fvm::euler_step(wp, k.dt, fw);
                     }
                     if (t == T) {
                         const size_t o = (size_t)r * pitch + gxs[m];

@@ -79,6 +79,8 @@ _SIGNATURES = {
     "gg_diagnostics_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _I32, _I32, _I32, _I32, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double, _VP, ctypes.POINTER(gg_diag)]),
     "gg_adjoint": (ctypes.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _DP, _I64]),
+    "gg_autotune": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(_I32)]),
+    "gg_set_plan": (ctypes.c_int, [_VP, _I32, _I32, _I32, _I32]),
     "gg_dt": (ctypes.c_double, [_VP]),
     "gg_dt_max": (ctypes.c_double, [_VP]),
     "gg_step_count": (_I64, [_VP]),
@@ -275,6 +277,15 @@ class GGSim:
 
     def step(self, nsteps: int):
         _check(gg_step(self._sim, nsteps), self._sim, "gg_step")
+
+    def set_plan(self, kind: str = "warp", T: int = 1, strip: int = 0, chunk: int = 0):
+        _check(lib().gg_set_plan(self._sim, 1 if kind == "warp" else 0, int(T), int(strip), int(chunk)),
+               self._sim, "gg_set_plan")
+
+    def autotune(self, trial_steps: int = 24) -> Dict:
+        chosen = (_I32 * 4)()
+        _check(lib().gg_autotune(self._sim, int(trial_steps), chosen), self._sim, "gg_autotune")
+        return dict(T=chosen[0], kind="warp" if chosen[1] == 1 else "smem", bx=chosen[2], by=chosen[3])
 
     def read(self, field: str = "v", fp64: bool = True, out=None):
         """Copy a field; into a new host numpy array, or into ``out`` (a

@@ -67,32 +67,60 @@ def test_ragged_and_degenerate_grids(nx, ny, precision):
         assert rel_err(g, r) <= TOL[precision], name
 
 
-@pytest.mark.parametrize("T", [1, 2, 3, 4, 5, 6, 7, 8])
-def test_temporal_blocking_matches_oracle(T):
-    """T steps per HBM pass: 29 steps (not a multiple of T) on a grid whose
-    strips and chunks have ragged tails."""
+PLANS = [("warp", T) for T in (1, 2, 3, 4)] + [("smem", T) for T in range(1, 9)]
+
+
+@pytest.mark.parametrize("kind,T", PLANS)
+def test_temporal_blocking_matches_oracle(kind, T):
+    """T steps per HBM pass with both kernels: 29 steps (not a multiple of T)
+    on a grid whose strips and chunks have ragged tails."""
     p = inputs.plain_128(300, 173, steps=29)
     p.u0, p.v0, p.w0 = inputs.random_state(300, 173, 5)
     s, ref = run_oracle(p, p.steps)
-    _, got = run_gpu(p, p.steps, "fp32_kahan", steps_per_pass=T)
+    with gg.GGSim.from_problem(p, precision="fp32_kahan") as sim:
+        sim.set_plan(kind, T, chunk=40)
+        sim.step(p.steps)
+        got = sim.state()
     for name, g, r in zip("uvw", got, ref):
         assert rel_err(g, r) <= 1e-5, name
 
 
 @pytest.mark.parametrize("precision", ["fp32_kahan", "fp32"])
-def test_temporal_blocking_is_bitwise_identical_across_T(precision):
-    """Each level of a temporally blocked pass runs the same per-cell
-    arithmetic as a single step, so every T gives the same bits."""
+def test_every_plan_is_bitwise_identical(precision):
+    """Each level of a temporally blocked pass, in either kernel, runs the
+    same per-cell arithmetic (rates_v) as a single step, so every plan gives
+    the same bits."""
     p = inputs.plain_128(200, 150, steps=24)
     p.u0, p.v0, p.w0 = inputs.random_state(200, 150, 9)
     base = None
-    for T in (1, 2, 3, 4, 6, 8):
-        _, got = run_gpu(p, p.steps, precision, steps_per_pass=T)
-        if base is None:
-            base = got
-        else:
-            for g, b in zip(got, base):
-                assert np.array_equal(g, b), f"T={T}"
+    for kind, T in PLANS:
+        for chunk in (0, 17):
+            with gg.GGSim.from_problem(p, precision=precision) as sim:
+                sim.set_plan(kind, T, chunk=chunk)
+                sim.step(p.steps)
+                got = sim.state(fp64=False)
+            if base is None:
+                base = got
+            else:
+                for g, b in zip(got, base):
+                    assert np.array_equal(g, b), (kind, T, chunk)
+
+
+def test_autotuner_keeps_the_state_and_the_bits():
+    p = inputs.plain_128(700, 520, steps=40)
+    p.u0, p.v0, p.w0 = inputs.random_state(700, 520, 19)
+    with gg.GGSim.from_problem(p, precision="fp32_kahan", steps_per_pass=1) as a:
+        before = a.state(fp64=False)
+        chosen = a.autotune(trial_steps=24)
+        assert chosen["T"] >= 1
+        for x, y in zip(before, a.state(fp64=False)):
+            assert np.array_equal(x, y)
+        a.step(40)
+        tuned = a.state(fp64=False)
+    with gg.GGSim.from_problem(p, precision="fp32_kahan", steps_per_pass=1) as b:
+        b.step(40)
+        for x, y in zip(tuned, b.state(fp64=False)):
+            assert np.array_equal(x, y)
 
 
 @pytest.mark.parametrize("state", [(1.0, 0.0, 0.0), (0.0, 1.0, 1.0), (0.0, 0.0, 0.0), (0.5, 1.0, 1.0)])
