@@ -38,7 +38,16 @@ using namespace gg;
 
 namespace {
 
-constexpr int kAdjBX = 32, kAdjBY = 8;
+// Geometry of the warp-marching adjoint launch: 30 written columns per warp,
+// chunks of adj_chunk() rows sized for about 16 warps per SM (152 SMs).
+constexpr int kAdjOut = 30;
+inline int adj_strips(int nx) { return (nx + kAdjOut - 1) / kAdjOut; }
+inline int adj_chunk(int nx, int ny)
+{
+    const int chunks = std::max(1, (16 * 152 + adj_strips(nx) - 1) / adj_strips(nx));
+    return std::min(128, std::max(8, (ny + chunks - 1) / chunks));
+}
+inline int adj_warps(int nx, int ny) { const int H = adj_chunk(nx, ny); return adj_strips(nx) * ((ny + H - 1) / H); }
 constexpr int kFlushEvery = 16;  // FP32 per-cell gradient sums are folded into FP64 this often
 
 struct AdjArgs {
@@ -59,116 +68,175 @@ __device__ __forceinline__ void kahan_add(float x, float inc, float comp, float&
     xo = t;
 }
 
-template <bool KAHAN>
-__global__ void __launch_bounds__(kAdjBX* kAdjBY) adjoint_step_kernel(const AdjArgs a, const Rates32 k)
-{
-    const int i = blockIdx.x * kAdjBX + threadIdx.x;
-    const int j = blockIdx.y * kAdjBY + threadIdx.y;
-    const int nx = a.nx, ny = a.ny, pitch = a.pitch;
-    double s_delta = 0.0, s_rho = 0.0, s_D = 0.0, s_c = 0.0;
-    if (i < nx && j < ny) {
-        const bool hasW = i > 0, hasE = i + 1 < nx, hasS = j > 0, hasN = j + 1 < ny;
-        const int iw = hasW ? i - 1 : i, ie = hasE ? i + 1 : i;
-        const int js = hasS ? j - 1 : j, jn = hasN ? j + 1 : j;
-#define L(f, x, y) __ldg((f) + (size_t)(y) * pitch + (x))
-        // lamW on the 3x3 neighbourhood (mirrored at the boundary).  With Kahan
-        // terms the stored value x and its compensation c represent x - c, so
-        // differences are taken as (x_a - x_b) - (c_a - c_b): the first part is
-        // exact for nearby values and the second restores the low-order bits
-        // that plain FP32 differences of a large smooth lam would lose.
-        auto cw = [&](int x, int y) { return KAHAN ? L(a.clw, x, y) : 0.0f; };
-        const float lwP0 = L(a.lw, i, j), cwP = cw(i, j);
-        auto rel = [&](int x, int y) { return (L(a.lw, x, y) - lwP0) - (cw(x, y) - cwP); };
-        // lamW relative to the centre cell: lwP = 0, neighbours carry the differences
-        const float lwP = 0.0f, lwE = rel(ie, j), lwW = rel(iw, j);
-        const float lwN = rel(i, jn), lwS = rel(i, js);
-        const float lwNE = rel(ie, jn), lwNW = rel(iw, jn), lwSE = rel(ie, js), lwSW = rel(iw, js);
-        const float a11P = L(a.a11, i, j), a11E = L(a.a11, ie, j), a11W = L(a.a11, iw, j);
-        const float a22P = L(a.a22, i, j), a22N = L(a.a22, i, jn), a22S = L(a.a22, i, js);
-        const float bP = L(a.a12, i, j), bE = L(a.a12, ie, j), bW = L(a.a12, iw, j);
-        const float bN = L(a.a12, i, jn), bS = L(a.a12, i, js);
-        // face differences of lamW seen from this cell (0 on boundary faces)
-        const float LxE = hasE ? lwP - lwE : 0.0f, LxW = hasW ? lwW - lwP : 0.0f;
-        const float LyN = hasN ? lwP - lwN : 0.0f, LyS = hasS ? lwS - lwP : 0.0f;
-        // Sx on rows j-1, j, j+1 of column i; Sy on columns i-1, i, i+1 of row j
-        auto sumx = [&](float c, float e, float w) { return (hasE ? c - e : 0.0f) + (hasW ? w - c : 0.0f); };
-        auto sumy = [&](float c, float n, float s) { return (hasN ? c - n : 0.0f) + (hasS ? s - c : 0.0f); };
-        const float SxP = bP * sumx(lwP, lwE, lwW);
-        const float SxN = bN * sumx(lwN, lwNE, lwNW);
-        const float SxS = bS * sumx(lwS, lwSE, lwSW);
-        const float SyP = bP * sumy(lwP, lwN, lwS);
-        const float SyE = bE * sumy(lwE, lwNE, lwSE);
-        const float SyW = bW * sumy(lwW, lwNW, lwSW);
-        const float Ty = (hasS ? SxS : 0.0f) - (hasN ? SxN : 0.0f) + SxP * ((hasN ? 0.0f : 1.0f) - (hasS ? 0.0f : 1.0f));
-        const float Tx = (hasW ? SyW : 0.0f) - (hasE ? SyE : 0.0f) + SyP * ((hasE ? 0.0f : 1.0f) - (hasW ? 0.0f : 1.0f));
-        const float D2T = ((a11P + a11E) * (lwE - lwP) + (a11W + a11P) * (lwW - lwP)) * k.kx +
-                          ((a22P + a22N) * (lwN - lwP) + (a22S + a22P) * (lwS - lwP)) * k.ky + (Tx + Ty) * k.kc;
+constexpr unsigned kFull = 0xffffffffu;
+__device__ __forceinline__ float from_west(float x) { return __shfl_up_sync(kFull, x, 1); }
+__device__ __forceinline__ float from_east(float x) { return __shfl_down_sync(kFull, x, 1); }
 
-        const float uP = L(a.u, i, j), uE = L(a.u, ie, j), uW = L(a.u, iw, j), uN = L(a.u, i, jn), uS = L(a.u, i, js);
-        const float vP = L(a.v, i, j), vE = L(a.v, ie, j), vW = L(a.v, iw, j), vN = L(a.v, i, jn), vS = L(a.v, i, js);
-        const float wP = L(a.w, i, j), wE = L(a.w, ie, j), wW = L(a.w, iw, j), wN = L(a.w, i, jn), wS = L(a.w, i, js);
-        const float luP = L(a.lu, i, j);
-        auto cv = [&](int x, int y) { return KAHAN ? L(a.clv, x, y) : 0.0f; };
-        const float lvP = L(a.lv, i, j), cvP = cv(i, j);
-        auto relv = [&](int x, int y) { return (L(a.lv, x, y) - lvP) - (cv(x, y) - cvP); };
-        // Table 1 pieces: mobility, V differences, lamV differences
-        const float mE = 1.0f - 0.5f * (uP + uE), mW = 1.0f - 0.5f * (uP + uW);
-        const float mN = 1.0f - 0.5f * (uP + uN), mS = 1.0f - 0.5f * (uP + uS);
-        const float dvE = vE - vP, dvW = vW - vP, dvN = vN - vP, dvS = vS - vP;
-        const float dlE = relv(ie, j), dlW = relv(iw, j), dlN = relv(i, jn), dlS = relv(i, js);
+// One row of the inputs of an adjoint step at one column.
+struct AdjRow {
+    float u, v, w, lu, lv, lw, clu, clv, clw, a11, a12, a22, g11, g12, g22;
+};
+
+// Adjoint step as a warp march: the warp owns 32 columns (30 written) and a
+// chunk of H rows, keeps rows q-1, q, q+1 of its inputs in registers (the
+// next row is fetched one row ahead) and takes east / west values by
+// shuffle.  The four rate gradients are summed per lane with FP32 Kahan sums
+// and folded into one FP64 record per warp at the end of the chunk.
+template <bool KAHAN, bool EDGE>
+__device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, const int H, const int strip,
+                                         const int chunk, const int lane, double* part)
+{
+    const int nx = a.nx, ny = a.ny, pitch = a.pitch;
+    const int gx = strip * 30 - 1 + lane;
+    const bool ind = EDGE ? (gx >= 0 && gx < nx) : true;
+    const bool hasW = EDGE ? gx > 0 : true, hasE = EDGE ? gx + 1 < nx : true;
+    const bool outc = ind && lane >= 1 && lane < 31;
+    const int ys = chunk * H;
+    const int ye = min(ny, ys + H);
+    auto load = [&](int r, AdjRow& x) {
+        if (ind && r >= 0 && r < ny) {
+            const size_t o = (size_t)r * pitch + gx;
+            x.u = __ldg(a.u + o); x.v = __ldg(a.v + o); x.w = __ldg(a.w + o);
+            x.lu = __ldg(a.lu + o); x.lv = __ldg(a.lv + o); x.lw = __ldg(a.lw + o);
+            if (KAHAN) {
+                x.clu = __ldg(a.clu + o); x.clv = __ldg(a.clv + o); x.clw = __ldg(a.clw + o);
+            } else {
+                x.clu = x.clv = x.clw = 0.0f;
+            }
+            x.a11 = __ldg(a.a11 + o); x.a12 = __ldg(a.a12 + o); x.a22 = __ldg(a.a22 + o);
+            x.g11 = a.g11[o]; x.g12 = a.g12[o]; x.g22 = a.g22[o];
+        } else {
+            x.u = x.v = x.w = x.lu = x.lv = x.lw = x.clu = x.clv = x.clw = 0.0f;
+            x.a11 = x.a12 = x.a22 = x.g11 = x.g12 = x.g22 = 0.0f;
+        }
+    };
+    // per-lane Kahan sums of the rate-gradient terms (delta, rho, D, c)
+    float acc[4] = {0.f, 0.f, 0.f, 0.f}, accc[4] = {0.f, 0.f, 0.f, 0.f};
+    auto accum = [&](int q, float x) {
+        const float y = __fsub_rn(x, accc[q]);
+        const float t = __fadd_rn(acc[q], y);
+        accc[q] = __fsub_rn(__fsub_rn(t, acc[q]), y);
+        acc[q] = t;
+    };
+
+    AdjRow S, P, N, nxt;
+    load(ys - 1, S);
+    load(ys, P);
+    load(ys + 1, N);
+    load(ys + 2, nxt);
+    for (int q = ys; q < ye; ++q) {
+        const bool hasS = q > 0, hasN = q + 1 < ny;
+        // compensated difference of lamW between two (value, Kahan term) pairs
+        auto dW = [](float la, float ca, float lb, float cb) { return __fsub_rn(__fsub_rn(la, lb), __fsub_rn(ca, cb)); };
+        // face differences of lamW on rows S, P, N (0 on boundary faces)
+        auto lx_e = [&](const AdjRow& X) {
+            float le = from_east(X.lw), ce = from_east(X.clw);
+            const float d = dW(X.lw, X.clw, le, ce);
+            return hasE ? d : 0.0f;
+        };
+        const float LxE_P = lx_e(P), LxE_N = lx_e(N), LxE_S = lx_e(S);
+        float LxW_P = from_west(LxE_P), LxW_N = from_west(LxE_N), LxW_S = from_west(LxE_S);
+        if (EDGE && !hasW) { LxW_P = LxW_N = LxW_S = 0.0f; }
+        const float LyN = hasN ? dW(P.lw, P.clw, N.lw, N.clw) : 0.0f;
+        const float LyS = hasS ? dW(S.lw, S.clw, P.lw, P.clw) : 0.0f;
+        // transpose of the a12 cross terms (mirrored central differences)
+        const float SxP = P.a12 * (LxE_P + LxW_P), SxN = N.a12 * (LxE_N + LxW_N), SxS = S.a12 * (LxE_S + LxW_S);
+        const float SyP = P.a12 * (LyN + LyS);
+        float SyE = from_east(SyP), SyW = from_west(SyP);
+        const float Ty = (hasS ? SxS : 0.0f) - (hasN ? SxN : 0.0f) + SxP * ((hasN ? 0.0f : 1.0f) - (hasS ? 0.0f : 1.0f));
+        float Tx;
+        if (EDGE) Tx = (hasW ? SyW : 0.0f) - (hasE ? SyE : 0.0f) + SyP * ((hasE ? 0.0f : 1.0f) - (hasW ? 0.0f : 1.0f));
+        else Tx = SyW - SyE;
+        float a11E = from_east(P.a11), a11W = from_west(P.a11);
+        if (EDGE) { if (!hasE) a11E = P.a11; if (!hasW) a11W = P.a11; }
+        const float a22N = hasN ? N.a22 : P.a22, a22S = hasS ? S.a22 : P.a22;
+        const float D2T = ((P.a11 + a11E) * (-LxE_P) + (a11W + P.a11) * LxW_P) * k.kx +
+                          ((P.a22 + a22N) * (-LyN) + (a22S + P.a22) * LyS) * k.ky + (Tx + Ty) * k.kc;
+
+        // state and lamV neighbourhood (mirrored at the boundary)
+        float uE = from_east(P.u), uW = from_west(P.u), vE = from_east(P.v), vW = from_west(P.v);
+        float wE = from_east(P.w), wW = from_west(P.w);
+        float lvE = from_east(P.lv), lvW = from_west(P.lv), cvE = from_east(P.clv), cvW = from_west(P.clv);
+        if (EDGE) {
+            if (!hasE) { uE = P.u; vE = P.v; wE = P.w; lvE = P.lv; cvE = P.clv; }
+            if (!hasW) { uW = P.u; vW = P.v; wW = P.w; lvW = P.lv; cvW = P.clv; }
+        }
+        const float uN = hasN ? N.u : P.u, uS = hasS ? S.u : P.u;
+        const float vN = hasN ? N.v : P.v, vS = hasS ? S.v : P.v;
+        const float wN = hasN ? N.w : P.w, wS = hasS ? S.w : P.w;
+        const float dlE = dW(lvE, cvE, P.lv, P.clv), dlW = dW(lvW, cvW, P.lv, P.clv);
+        const float dlN = hasN ? dW(N.lv, N.clv, P.lv, P.clv) : 0.0f, dlS = hasS ? dW(S.lv, S.clv, P.lv, P.clv) : 0.0f;
+        const float mE = 1.0f - 0.5f * (P.u + uE), mW = 1.0f - 0.5f * (P.u + uW);
+        const float mN = 1.0f - 0.5f * (P.u + uN), mS = 1.0f - 0.5f * (P.u + uS);
+        const float dvE = vE - P.v, dvW = vW - P.v, dvN = vN - P.v, dvS = vS - P.v;
         const float d1 = (mE * dvE + mW * dvW) * k.ihx2 + (mN * dvN + mS * dvS) * k.ihy2;
         const float d1T = (mE * dlE + mW * dlW) * k.ihx2 + (mN * dlN + mS * dlS) * k.ihy2;
         const float dU = 0.5f * ((dvE * dlE + dvW * dlW) * k.ihx2 + (dvN * dlN + dvS * dlS) * k.ihy2);
 
-        float fu, fv, fw;
+        float fu, fvv, fw;
         if (k.no_reaction) {
             fu = k.D * dU;
-            fv = k.D * d1T;
+            fvv = k.D * d1T;
             fw = D2T;
         } else {
-            fu = (1.0f - 2.0f * uP - k.delta * wP) * luP + k.D * dU;
-            fv = k.rho * (1.0f - 2.0f * vP) * lvP + k.D * d1T + k.c * lwP0;
-            fw = -k.delta * uP * luP - k.c * lwP0 + D2T;
-            s_delta = -(double)luP * (double)uP * (double)wP;
-            s_rho = (double)lvP * (double)vP * (1.0 - (double)vP);
-            s_c = (double)lwP0 * ((double)vP - (double)wP);
+            fu = (1.0f - 2.0f * P.u - k.delta * P.w) * P.lu + k.D * dU;
+            fvv = k.rho * (1.0f - 2.0f * P.v) * P.lv + k.D * d1T + k.c * P.lw;
+            fw = -k.delta * P.u * P.lu - k.c * P.lw + D2T;
         }
-        s_D = (double)lvP * (double)d1;
-        const size_t o = (size_t)j * pitch + i;
-        if constexpr (KAHAN) {
-            float x, cx;
-            kahan_add(luP, k.dt * fu, a.clu[o], x, cx); a.luo[o] = x; a.cluo[o] = cx;
-            kahan_add(lvP, k.dt * fv, cvP, x, cx); a.lvo[o] = x; a.clvo[o] = cx;
-            kahan_add(lwP0, k.dt * fw, cwP, x, cx); a.lwo[o] = x; a.clwo[o] = cx;
-        } else {
-            a.luo[o] = luP + k.dt * fu;
-            a.lvo[o] = lvP + k.dt * fv;
-            a.lwo[o] = lwP0 + k.dt * fw;
+        // fetch the row after N while this row is finished
+        AdjRow nn;
+        load(q + 3, nn);
+        if (outc) {
+            const size_t o = (size_t)q * pitch + gx;
+            if (!k.no_reaction) {
+                accum(0, -P.lu * P.u * P.w);
+                accum(1, P.lv * P.v * (1.0f - P.v));
+                accum(3, P.lw * (P.v - P.w));
+            }
+            accum(2, P.lv * d1);
+            if (KAHAN) {
+                float x, cx;
+                kahan_add(P.lu, k.dt * fu, P.clu, x, cx); a.luo[o] = x; a.cluo[o] = cx;
+                kahan_add(P.lv, k.dt * fvv, P.clv, x, cx); a.lvo[o] = x; a.clvo[o] = cx;
+                kahan_add(P.lw, k.dt * fw, P.clw, x, cx); a.lwo[o] = x; a.clwo[o] = cx;
+            } else {
+                a.luo[o] = P.lu + k.dt * fu;
+                a.lvo[o] = P.lv + k.dt * fvv;
+                a.lwo[o] = P.lw + k.dt * fw;
+            }
+            a.g11[o] = P.g11 + k.dt * (((wE - P.w) * LxE_P + (P.w - wW) * LxW_P) * k.kx);
+            a.g22[o] = P.g22 + k.dt * (((wN - P.w) * LyN + (P.w - wS) * LyS) * k.ky);
+            a.g12[o] = P.g12 + k.dt * (((LxE_P + LxW_P) * (wN - wS) + (LyN + LyS) * (wE - wW)) * k.kc);
         }
-        // tensor gradients (FP32 sums, folded into FP64 every kFlushEvery steps)
-        a.g11[o] += k.dt * (((wE - wP) * LxE + (wP - wW) * LxW) * k.kx);
-        a.g22[o] += k.dt * (((wN - wP) * LyN + (wP - wS) * LyS) * k.ky);
-        a.g12[o] += k.dt * (((LxE + LxW) * (wN - wS) + (LyN + LyS) * (wE - wW)) * k.kc);
-#undef L
+        S = P;
+        P = N;
+        N = nxt;
+        nxt = nn;
     }
-    // FP64 block reduction of the rate gradients, accumulated per block
-    __shared__ double sh[4][kAdjBX * kAdjBY / 32];
-    double s4[4] = {s_delta, s_rho, s_D, s_c};
-    for (int q = 0; q < 4; ++q)
-        for (int off = 16; off > 0; off >>= 1) s4[q] += __shfl_xor_sync(0xffffffffu, s4[q], off);
-    const int tid = threadIdx.y * kAdjBX + threadIdx.x;
-    if ((tid & 31) == 0)
-        for (int q = 0; q < 4; ++q) sh[q][tid >> 5] = s4[q];
-    __syncthreads();
-    if (tid == 0) {
-        double* p = a.partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4;
+    // fold the per-lane sums into this warp's FP64 record (fixed order)
+    double s4[4];
+    for (int qq = 0; qq < 4; ++qq) {
+        s4[qq] = (double)acc[qq] - (double)accc[qq];
+        for (int off = 16; off > 0; off >>= 1) s4[qq] += __shfl_xor_sync(kFull, s4[qq], off);
+    }
+    if (lane == 0) {
         const double dtd = (double)k.dt;
-        for (int q = 0; q < 4; ++q) {
-            double t = 0.0;
-            for (int wq = 0; wq < kAdjBX * kAdjBY / 32; ++wq) t += sh[q][wq];
-            p[q] += dtd * t;
-        }
+        for (int qq = 0; qq < 4; ++qq) part[qq] += dtd * s4[qq];
     }
+}
+
+template <bool KAHAN>
+__global__ void __launch_bounds__(128) adjoint_step_kernel(const AdjArgs a, const Rates32 k, const int H,
+                                                           const int nstrips, const int nwarps)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gw >= nwarps) return;
+    const int strip = gw % nstrips, chunk = gw / nstrips;
+    const int gx0 = strip * 30 - 1;
+    double* part = a.partials + (size_t)gw * 4;
+    if (gx0 >= 1 && gx0 + 31 <= a.nx - 2) adj_warp<KAHAN, false>(a, k, H, strip, chunk, lane, part);
+    else adj_warp<KAHAN, true>(a, k, H, strip, chunk, lane, part);
 }
 
 // g64 += g32; g32 = 0 (pitched, 3 fields)
@@ -237,8 +305,7 @@ static int adj_workspace(gg_sim* s, int K, int nseg, bool kahan, AdjWork** out)
     const size_t fb = ((size_t)s->pitch * s->ny * 4 + 255) / 256 * 256;
     const size_t db = ((size_t)s->pitch * s->ny * 8 + 255) / 256 * 256;
     const int nstate = kahan ? 6 : 3;
-    const dim3 grid((s->nx + kAdjBX - 1) / kAdjBX, (s->ny + kAdjBY - 1) / kAdjBY);
-    const int nblocks = grid.x * grid.y;
+    const int nblocks = adj_warps(s->nx, s->ny);  // one FP64 record of rate gradients per warp
     const size_t need = fb * ((size_t)nseg * nstate + (size_t)K * 3 + 6 + 12 + 3) + db * 3 +
                         (((size_t)nblocks * 4 * 8 + 255) / 256 * 256);
     AdjWork* w = (AdjWork*)s->adj;
@@ -323,8 +390,8 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
     const Rates32 r = rates32(s);
     Plan32 plan1 = s->plan;
     plan1.T = 1;
-    const dim3 agrid((s->nx + kAdjBX - 1) / kAdjBX, (s->ny + kAdjBY - 1) / kAdjBY);
-    const dim3 ablock(kAdjBX, kAdjBY);
+    const int aH = adj_chunk(s->nx, s->ny), astrips = adj_strips(s->nx), awarps = adj_warps(s->nx, s->ny);
+    const int ablocks = (awarps + 3) / 4;
     int lb = 0;          // current lam buffer
     int since_flush = 0;
     auto flush = [&]() {
@@ -366,8 +433,8 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
             a.g11 = w->g32[0]; a.g12 = w->g32[1]; a.g22 = w->g32[2];
             a.partials = w->partials;
             a.nx = s->nx; a.ny = s->ny; a.pitch = s->pitch;
-            if (kahan) adjoint_step_kernel<true><<<agrid, ablock, 0, st>>>(a, r);
-            else adjoint_step_kernel<false><<<agrid, ablock, 0, st>>>(a, r);
+            if (kahan) adjoint_step_kernel<true><<<ablocks, 128, 0, st>>>(a, r, aH, astrips, awarps);
+            else adjoint_step_kernel<false><<<ablocks, 128, 0, st>>>(a, r, aH, astrips, awarps);
             e = cudaGetLastError();
             lb ^= 1;
             if (e == cudaSuccess && ++since_flush == kFlushEvery) e = flush();
