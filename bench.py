@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--steps-per-pass", type=int, default=0)
     ap.add_argument("--fp64-time-steps", type=int, default=100)
     ap.add_argument("--adjoint-steps", type=int, default=10000)
+    ap.add_argument("--ensemble-steps", type=int, default=5000)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / adjoint / CPU legs")
     return ap.parse_args()
 
@@ -203,6 +204,32 @@ def cpu_baseline_leg(p):
             "sample": f"{n} explicit steps of the {p.nx}x{p.ny} grid ({el:.1f} s)"}
 
 
+def profiled_traffic(kernel_key: str, cells: int):
+    """DRAM bytes per launch of `kernel_key` from profiles/dram_traffic.txt
+    (one ncu capture, scaled to `cells` by the cells processed), or None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.startswith(kernel_key + " "):
+                    kv = dict(x.split("=") for x in line.split()[1:] if "=" in x)
+                    return int(kv["total"]) * cells / int(kv["cells"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+def timed_steps(sim, n, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    sim.step(n)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
 def run_ours(args, dist):
     import torch
     from paper_2006_01748_gb300 import build, gg, inputs
@@ -212,19 +239,17 @@ def run_ours(args, dist):
     stream = torch.cuda.current_stream(dev)
     p = inputs.hetero_8192(nx=args.nx, steps=args.time_steps, seed=inputs.SEED_HETERO_8192 + dist.rank)
     sim = gg.GGSim.from_problem(p, precision="fp32_kahan", steps_per_pass=args.steps_per_pass)
-    T = sim.steps_per_pass
+    plan = sim.plan()
+    T = plan["T"]
     n_inner = args.time_steps
-    launches_per_step = -(-n_inner // T) + 2  # step passes + diagnostics partial/final
-
-    def one_step():
-        sim.step(n_inner)
-        rc, d = gg.gg_diagnostics(sim.handle)
-        if rc not in (gg.GG_OK,):
-            raise RuntimeError(f"diagnostics failed: {rc} {gg.gg_last_error(sim.handle)}")
-        return d
+    passes = -(-n_inner // T)
+    launches_per_step = passes + 2  # step passes + diagnostics partial/final
 
     for _ in range(args.warmup):
-        one_step()
+        sim.step(n_inner)
+        rc, _d = gg.gg_diagnostics(sim.handle)
+        if rc != gg.GG_OK:
+            raise RuntimeError(f"diagnostics failed: {rc} {gg.gg_last_error(sim.handle)}")
     torch.cuda.synchronize()
 
     # timed region: K bench steps bracketed by barrier + synchronize
@@ -234,6 +259,7 @@ def run_ours(args, dist):
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kev = []
+    torch.cuda.nvtx.range_push("timed")
     ev0.record(stream)
     for _ in range(args.steps):
         a = torch.cuda.Event(enable_timing=True)
@@ -242,75 +268,71 @@ def run_ours(args, dist):
         sim.step(n_inner)
         b.record(stream)
         kev.append((a, b))
-        rc, d = gg.gg_diagnostics(sim.handle)
+        gg.gg_diagnostics(sim.handle)
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     dist.barrier()
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     ms_max = dist.max(ms)
     step_ms = [a.elapsed_time(b) for a, b in kev]
-    passes = -(-n_inner // T)
     launch_ms = statistics.mean(step_ms) / passes
     value = p.cells * n_inner * args.steps * dist.world / (ms_max / 1e3)
 
     peak, peak_kind = measured_peaks()
+    kname = f"stepw_kernel<T={T},Kahan>" if plan["kind"] == "warp" else f"step32_kernel<T={T},Kahan>"
     alg_bytes = BYTES_PER_CELL_PASS["fp32_kahan"] * p.cells
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    traffic = profiled_traffic(f"{plan['kind']} T={T} kahan chunk={plan['by']}", p.cells)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_kind": peak_kind, "kernel": f"step32_kernel<T={T}, Kahan>",
-                "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": launch_ms}
+                "traffic": traffic, "peak_kind": peak_kind, "kernel": kname, "chunk_rows": plan["by"],
+                "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": launch_ms,
+                "note": "one launch = one pass of T explicit steps: 60 B/cell of state and tensor traffic"}
 
     extras = {}
     if not args.no_extras:
+        # the same step with one step per pass (the HBM-bound configuration)
+        for name, prec in (("fp32_kahan_T1", "fp32_kahan"), ("fp32_T1", "fp32")):
+            s2 = gg.GGSim.from_problem(p, precision=prec, steps_per_pass=1)
+            s2.step(20)
+            n2 = 200
+            ms2 = timed_steps(s2, n2, stream)
+            pl2 = s2.plan()
+            s2.close()
+            bpc = BYTES_PER_CELL_PASS[prec]
+            ach2 = bpc * p.cells / (ms2 / 1e3 / n2) / 1e9
+            extras[name] = {"value": p.cells * n2 / (ms2 / 1e3), "unit": "cell-updates/s",
+                            "roofline": {"bound": "hbm", "achieved": ach2, "peak": peak, "unit": "GB/s",
+                                         "frac": ach2 / peak, "kernel": f"stepw_kernel<T=1,{prec}>",
+                                         "chunk_rows": pl2["by"],
+                                         "traffic": profiled_traffic(f"warp T=1 {'kahan' if prec == 'fp32_kahan' else 'plain'}"
+                                                                     f" chunk={pl2['by']}", p.cells)}}
         # plain FP64 step on the same grid (fewer time steps; throughput is per cell-update)
         sim64 = gg.GGSim.from_problem(p, precision="fp64")
         sim64.step(5)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        sim64.step(args.fp64_time_steps)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms64 = a.elapsed_time(b)
+        ms64 = timed_steps(sim64, args.fp64_time_steps, stream)
         sim64.close()
         v64 = p.cells * args.fp64_time_steps / (ms64 / 1e3)
         extras["fp64_plain"] = {"value": v64, "unit": "cell-updates/s", "time_steps": args.fp64_time_steps,
                                 "hbm_frac": 72 * p.cells / (ms64 / 1e3 / args.fp64_time_steps) / 1e9 / peak,
                                 "fp32_over_fp64": value / dist.world / v64}
-        # fused FP32 without Kahan and with T = 1 (single HBM pass per step)
-        for name, prec, spp in (("fp32_kahan_T1", "fp32_kahan", 1), ("fp32_T1", "fp32", 1)):
-            s2 = gg.GGSim.from_problem(p, precision=prec, steps_per_pass=spp)
-            s2.step(20)
-            torch.cuda.synchronize()
-            a.record(stream)
-            s2.step(200)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms2 = a.elapsed_time(b)
-            s2.close()
-            v2 = p.cells * 200 / (ms2 / 1e3)
-            extras[name] = {"value": v2, "unit": "cell-updates/s",
-                            "hbm_frac": BYTES_PER_CELL_PASS[prec] * p.cells / (ms2 / 1e3 / 200) / 1e9 / peak}
-
-    if not args.no_extras:
-        # adjoint / forward time on the 2048 x 2048 adjoint workload (10^4 steps,
-        # sqrt(N) checkpointing): the forward solve as gg_step runs it, and the
-        # whole gg_adjoint call (its own forward pass, recompute, reverse sweep)
+        # adjoint / forward on the 2048 x 2048 adjoint workload (10^4 steps,
+        # sqrt(N) checkpointing): the forward solve as gg_step runs it (tuned
+        # plan), and the whole gg_adjoint call (its own forward pass, the
+        # recomputation of every segment, the reverse sweep)
         pa = inputs.adjoint_2048(steps=args.adjoint_steps)
-        simf = gg.GGSim.from_problem(pa, precision="fp32_kahan", steps_per_pass=args.steps_per_pass)
-        simf.step(50)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        simf.step(pa.steps)
-        b.record(stream)
-        torch.cuda.synchronize()
-        fwd_ms = a.elapsed_time(b)
+        simf = gg.GGSim.from_problem(pa, precision="fp32_kahan")
+        simf.step(48)
+        fwd_ms = timed_steps(simf, pa.steps, stream)
         Vn = torch.empty(pa.cells, dtype=torch.float32, device=dev)
         simf.read("v", out=Vn)
         simf.close()
-        sima = gg.GGSim.from_problem(pa, precision="fp32_kahan", steps_per_pass=args.steps_per_pass)
+        simt = gg.GGSim.from_problem(pa, precision="fp32_kahan", steps_per_pass=1)
+        simt.step(48)
+        fwd1_ms = timed_steps(simt, pa.steps, stream)
+        simt.close()
+        sima = gg.GGSim.from_problem(pa, precision="fp32_kahan")
         dLdv = (Vn / pa.cells).contiguous()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -318,21 +340,39 @@ def run_ours(args, dist):
         adj_ms = 1e3 * (time.perf_counter() - t0)
         sima.close()
         extras["adjoint"] = {"workload": f"adjoint_2048: {pa.nx}x{pa.ny}, {pa.steps} steps, sqrt(N) checkpoints",
-                             "forward_ms": fwd_ms, "adjoint_ms": adj_ms, "adjoint_over_forward": adj_ms / fwd_ms}
+                             "forward_ms": fwd_ms, "forward_T1_ms": fwd1_ms, "adjoint_ms": adj_ms,
+                             "adjoint_over_forward": adj_ms / fwd_ms, "adjoint_over_forward_T1": adj_ms / fwd1_ms}
+        # batched ensemble: 256 uneven instances, one persistent graph-captured launch
+        specs = inputs.ensemble_specs(256)
+        probs = [inputs.ensemble_instance(k, specs[k], steps=args.ensemble_steps) for k in range(256)]
+        with gg.GGBatch(probs) as bt:
+            tuned = bt.autotune(trial_steps=8)
+            bt.step(args.ensemble_steps)  # captures the graph and warms up
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bt.step(args.ensemble_steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ens_ms = a.elapsed_time(b)
+            info = bt.launch_info()
+        ens_cells = sum(q.cells for q in probs)
+        extras["ensemble"] = {"workload": f"256 instances, grids from {{128..1024}}^2, {args.ensemble_steps} steps",
+                              "cells": ens_cells, "value": ens_cells * args.ensemble_steps / (ens_ms / 1e3),
+                              "unit": "cell-updates/s", "plan": tuned, "graph": info["graph"], "ctas": info["ctas"],
+                              "hbm_frac": 60 * ens_cells * args.ensemble_steps / tuned["T"] / (ens_ms / 1e3) / 1e9 / peak}
 
     # end to end through the public API with host buffers: create from host
     # arrays (H2D), advance, read the three fields back (D2H)
-    e2e_steps = 1
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        s3 = gg.GGSim.from_problem(p, precision="fp32_kahan", steps_per_pass=args.steps_per_pass)
-        s3.step(n_inner)
-        out = s3.state(fp64=False)
-        s3.close()
+    s3 = gg.GGSim.from_problem(p, precision="fp32_kahan", steps_per_pass=args.steps_per_pass)
+    s3.step(n_inner)
+    out = s3.state(fp64=False)
+    s3.close()
     torch.cuda.synchronize()
     e2e_el = time.perf_counter() - t0
-    e2e = {"value": p.cells * n_inner * e2e_steps / e2e_el, "unit": "cell-updates/s",
+    e2e = {"value": p.cells * n_inner / e2e_el, "unit": "cell-updates/s",
            "h2d_bytes_per_step": 6 * 8 * p.cells, "d2h_bytes_per_step": 3 * 4 * p.cells}
 
     if dist.rank == 0:

@@ -218,6 +218,11 @@ int gg_autotune(gg_sim* sim, int64_t trial_steps, int32_t* chosen);
  * GG_ERR_ARG for values out of range, GG_ERR_STATE for GG_FP64_PLAIN. */
 int gg_set_plan(gg_sim* sim, int32_t kind, int32_t T, int32_t strip, int32_t chunk);
 
+/* Launch plan in use: info[0..3] = kernel (1 warp-register wavefront,
+ * 0 shared-memory wavefront, 2 plain FP64), steps per pass T, strip width,
+ * chunk height. */
+int gg_plan_info(const gg_sim* sim, int32_t* info);
+
 double gg_dt(const gg_sim* sim);              /* fixed dt (0 if sim is NULL) */
 double gg_dt_max(const gg_sim* sim);          /* stable bound dt_max */
 int64_t gg_step_count(const gg_sim* sim);     /* steps taken so far */
@@ -260,11 +265,11 @@ int gg_batch_read(gg_batch* b, int32_t inst, int32_t field, void* dst,
 int gg_batch_diagnostics(gg_batch* b, int32_t inst, gg_diag* out);
 
 /* Autotuner of the ensemble launch: times trial_steps steps (>= 1; 0 means
- * 8) of every candidate tile shape -- strip width bx in {128, 256}, chunk
- * height by in {32, 64, 128} (by >= 8T) and steps per pass T in {1, 2, 4} --
- * on the batch itself, keeps the fastest, and restores the state it
- * advanced.  chosen (may be NULL) receives {T, bx, by, threads}.
- * Synchronizes. */
+ * 8) of every candidate tile shape -- steps per pass T in {1, 2, 3, 4} and
+ * chunk height by in {32, 64, 128} rows (by >= 4T + 8) of the warp tiles,
+ * whose strips are 32 - 2T columns wide -- on the batch itself, keeps the
+ * fastest, and restores the state it advanced.  chosen (may be NULL)
+ * receives {T, strip width, by, threads per CTA}.  Synchronizes. */
 int gg_batch_autotune(gg_batch* b, int64_t trial_steps, int32_t* chosen);
 
 /* Testing hook for the bounded barrier wait: sets the per-wait time limit

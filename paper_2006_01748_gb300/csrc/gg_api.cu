@@ -598,6 +598,17 @@ int gg_set_plan(gg_sim* s, int32_t kind, int32_t T, int32_t strip, int32_t chunk
     return GG_OK;
 }
 
+int gg_plan_info(const gg_sim* s, int32_t* info)
+{
+    if (!s || !info) return GG_ERR_ARG;
+    const bool fp64 = s->params.precision == GG_FP64_PLAIN;
+    info[0] = fp64 ? 2 : s->plan.kind;
+    info[1] = fp64 ? 1 : s->plan.T;
+    info[2] = fp64 ? 32 : s->plan.bx;
+    info[3] = fp64 ? 8 : s->plan.by;
+    return GG_OK;
+}
+
 int gg_destroy(gg_sim* s)
 {
     if (!s) return GG_OK;

@@ -1,12 +1,13 @@
 // Ensembles: many independent grids (their own size, rates, dt and tensor
 // field) advanced by one persistent, cooperative, graph-captured launch.
 //
-// Work decomposition.  Every instance is cut into the same kind of tiles as
-// the single-grid FP32 step (strips of bx columns, chunks of by rows); the
-// tiles of all instances form one work list.  A persistent CTA walks the list
-// with a grid stride, runs one pass of T steps on each tile (tile_pass of
-// gg_step32.cuh), then all CTAs meet at a grid barrier before the next pass
-// reads the state the previous pass wrote.  The barrier is a counter plus a
+// Work decomposition.  Every instance is cut into the warp tiles of the
+// single-grid warp-register wavefront (strips of 32 - 2T columns, chunks of
+// H rows); the tiles of all instances form one work list.  Each warp of a
+// persistent CTA walks the list with a grid stride and runs one pass of T
+// steps on each tile (warp_pass of gg_stepw.cuh, with L1-bypassing state
+// loads), then all CTAs meet at a grid barrier before the next pass reads
+// the state the previous pass wrote.  The barrier is a counter plus a
 // generation word in global memory; a CTA that waits longer than the
 // barrier timeout sets the device error word and leaves, so a wait can
 // never hang the GPU: the next synchronizing call reports GG_ERR_TIMEOUT.
@@ -20,16 +21,16 @@
 #include <vector>
 
 #include "gg_sim.cuh"
-#include "gg_step32.cuh"
+#include "gg_stepw.cuh"
 
 using namespace gg;
 
 namespace {
 
 struct InstDesc {
-    Grid32 g[2];  // g[p]: pass reading buffer p and writing buffer p ^ 1
+    Grid32 g[2];    // g[p]: pass reading buffer p and writing buffer p ^ 1
     Rates32 r;
-    int strips, chunks;
+    int strips[2];  // warp strips for the plan's T (0) and for T = 1 (1)
 };
 
 struct InstHost {
@@ -77,51 +78,48 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned e
     return *s_ok != 0;
 }
 
-template <int T, bool KAHAN, int MAXM>
-__global__ void __launch_bounds__(256) batch_kernel(const InstDesc* __restrict__ desc, const int2* __restrict__ items,
-                                                    int nitems, int npasses, int parity0, int bx, int by, int halo,
-                                                    int sw, unsigned* bar, int* err, unsigned expected,
+template <int T, bool KAHAN>
+__global__ void __launch_bounds__(128) batch_kernel(const InstDesc* __restrict__ desc, const int2* __restrict__ items,
+                                                    int nitems, int npasses, int parity0, int variant, int H,
+                                                    unsigned* bar, int* err, unsigned expected,
                                                     unsigned long long timeout_ns)
 {
-    extern __shared__ float smem[];
     __shared__ int s_ok;
     __shared__ unsigned s_gen;
     if (threadIdx.x == 0) s_gen = atomicAdd(&bar[1], 0u);
     __syncthreads();
     unsigned gen = s_gen;
+    constexpr int OUT = 32 - 2 * T;
+    const int lane = threadIdx.x & 31;
+    const int wpc = blockDim.x >> 5;
     for (int pass = 0; pass < npasses; ++pass) {
         const int parity = (parity0 + pass) & 1;
-        for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        for (int w = blockIdx.x * wpc + (threadIdx.x >> 5); w < nitems; w += gridDim.x * wpc) {
             const int2 it = items[w];
             const InstDesc& d = desc[it.x];
-            const int sx = it.y % d.strips, sy = it.y / d.strips;
-            step32::tile_pass<T, KAHAN, MAXM, true>(d.g[parity], d.r, bx, by, halo, sw, sx, sy, smem);
+            const int strips = d.strips[variant];
+            const int sx = it.y % strips, sy = it.y / strips;
+            const int gx0 = sx * OUT - T;
+            if (gx0 >= 1 && gx0 + 31 <= d.g[parity].nx - 2)
+                stepw::warp_pass<T, KAHAN, false, true>(d.g[parity], d.r, H, sx, sy, lane);
+            else
+                stepw::warp_pass<T, KAHAN, true, true>(d.g[parity], d.r, H, sx, sy, lane);
         }
         if (pass + 1 < npasses && !grid_barrier(bar, err, expected, gen, timeout_ns, &s_ok)) return;
     }
 }
 
-typedef void (*BatchKernel)(const InstDesc*, const int2*, int, int, int, int, int, int, int, unsigned*, int*, unsigned,
+typedef void (*BatchKernel)(const InstDesc*, const int2*, int, int, int, int, int, unsigned*, int*, unsigned,
                             unsigned long long);
 
-template <int T, bool KAHAN>
-BatchKernel pick_maxm(int maxm)
-{
-    switch (maxm) {
-        case 1: return batch_kernel<T, KAHAN, 1>;
-        case 2: return batch_kernel<T, KAHAN, 2>;
-        default: return batch_kernel<T, KAHAN, 3>;
-    }
-}
-
 template <bool KAHAN>
-BatchKernel pick(int T, int maxm)
+BatchKernel pick(int T)
 {
     switch (T) {
-        case 1: return pick_maxm<1, KAHAN>(maxm);
-        case 2: return pick_maxm<2, KAHAN>(maxm);
-        case 3: return pick_maxm<3, KAHAN>(maxm);
-        default: return pick_maxm<4, KAHAN>(maxm);
+        case 1: return batch_kernel<1, KAHAN>;
+        case 2: return batch_kernel<2, KAHAN>;
+        case 3: return batch_kernel<3, KAHAN>;
+        default: return batch_kernel<4, KAHAN>;
     }
 }
 
@@ -141,8 +139,8 @@ struct gg_batch {
     std::vector<InstHost> inst;
     void* arena = nullptr;
     InstDesc* d_desc = nullptr;
-    int2* d_items = nullptr;
-    int nitems = 0;
+    int2* d_items[2] = {nullptr, nullptr};  // work lists for the plan's T and for T = 1
+    int nitems[2] = {0, 0};
     unsigned* d_bar = nullptr;  // [count, generation]
     int* d_err = nullptr;
     double* d_partials = nullptr;
@@ -167,10 +165,12 @@ int batch_fail(gg_batch* b, cudaError_t e, const char* where)
     return GG_ERR_CUDA;
 }
 
-void build_desc(gg_batch* b, std::vector<InstDesc>& desc, std::vector<int2>& items)
+void build_desc(gg_batch* b, std::vector<InstDesc>& desc, std::vector<int2> items[2])
 {
     desc.resize(b->n);
-    items.clear();
+    items[0].clear();
+    items[1].clear();
+    const int outs[2] = {32 - 2 * b->plan.T, 30};
     for (int k = 0; k < b->n; ++k) {
         const InstHost& h = b->inst[k];
         InstDesc& d = desc[k];
@@ -193,9 +193,11 @@ void build_desc(gg_batch* b, std::vector<InstDesc>& desc, std::vector<int2>& ite
         r.kc = (float)(0.25 / (h.dx * h.dy));
         r.ihx2 = (float)(1.0 / (h.dx * h.dx)); r.ihy2 = (float)(1.0 / (h.dy * h.dy));
         r.no_reaction = (h.params.flags & GG_FLAG_NO_REACTION) ? 1 : 0;
-        d.strips = (h.nx + b->plan.bx - 1) / b->plan.bx;
-        d.chunks = (h.ny + b->plan.by - 1) / b->plan.by;
-        for (int t = 0; t < d.strips * d.chunks; ++t) items.push_back(make_int2(k, t));
+        const int chunks = (h.ny + b->plan.by - 1) / b->plan.by;
+        for (int v = 0; v < 2; ++v) {
+            d.strips[v] = (h.nx + outs[v] - 1) / outs[v];
+            for (int t = 0; t < d.strips[v] * chunks; ++t) items[v].push_back(make_int2(k, t));
+        }
     }
 }
 
@@ -207,16 +209,20 @@ int configure(gg_batch* b, const Plan32& plan)
 {
     b->plan = plan;
     std::vector<InstDesc> desc;
-    std::vector<int2> items;
+    std::vector<int2> items[2];
     build_desc(b, desc, items);
-    if (b->d_items) cudaFree(b->d_items);
-    b->d_items = nullptr;
-    cudaError_t e = cudaMalloc(&b->d_items, std::max<size_t>(items.size(), 1) * sizeof(int2));
-    if (e != cudaSuccess) { cudaGetLastError(); b->last_error = "work list allocation failed"; return GG_ERR_OOM; }
-    b->nitems = (int)items.size();
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < 2; ++v) {
+        if (b->d_items[v]) cudaFree(b->d_items[v]);
+        b->d_items[v] = nullptr;
+        e = cudaMalloc(&b->d_items[v], std::max<size_t>(items[v].size(), 1) * sizeof(int2));
+        if (e != cudaSuccess) { cudaGetLastError(); b->last_error = "work list allocation failed"; return GG_ERR_OOM; }
+        b->nitems[v] = (int)items[v].size();
+    }
     e = cudaMemcpyAsync(b->d_desc, desc.data(), desc.size() * sizeof(InstDesc), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream);
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v)
+        e = cudaMemcpyAsync(b->d_items[v], items[v].data(), items[v].size() * sizeof(int2), cudaMemcpyHostToDevice,
+                            b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return batch_fail(b, e, "batch configure");
     for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
@@ -237,43 +243,34 @@ int occupancy_ctas(gg_batch* b, BatchKernel k, size_t smem, int threads, int* ou
     return GG_OK;
 }
 
-BatchKernel kernel_for(const gg_batch* b, int T, size_t* smem_out)
-{
-    const Plan32& p = b->plan;
-    const int sw = p.bx + 2 * p.halo;
-    const int maxm = (sw + p.threads - 1) / p.threads;
-    *smem_out = (size_t)sw * sizeof(float) * (T * 9 + (b->kahan ? T * 6 : 0) + 3 * (T + 2));
-    return b->kahan ? pick<true>(T, maxm) : pick<false>(T, maxm);
-}
+BatchKernel kernel_for(const gg_batch* b, int T) { return b->kahan ? pick<true>(T) : pick<false>(T); }
 
-// Sets the shared-memory attribute of the kernels for every T <= plan.T and
-// sizes their persistent grids from the occupancy.  Called outside stream
-// capture: during capture only kernel launches are enqueued.
+// Sizes the persistent grids of the kernels for the plan's T and for T = 1
+// from their occupancy.  Called outside stream capture: during capture only
+// kernel launches are enqueued.
 int prepare_kernels(gg_batch* b)
 {
-    for (int T = 1; T <= b->plan.T; ++T) {
-        size_t smem = 0;
-        BatchKernel k = kernel_for(b, T, &smem);
+    const int Ts[2] = {b->plan.T, 1};
+    for (int v = 0; v < 2; ++v) {
         int ctas = 0;
-        int rc = occupancy_ctas(b, k, smem, b->plan.threads, &ctas);
+        int rc = occupancy_ctas(b, kernel_for(b, Ts[v]), 0, b->plan.threads, &ctas);
         if (rc != GG_OK) return rc;
-        b->ctas_for_T[T] = std::min(ctas, std::max(b->nitems, 1));
+        const int warps_per_cta = b->plan.threads / 32;
+        b->ctas_for_T[Ts[v]] = std::min(ctas, std::max((b->nitems[v] + warps_per_cta - 1) / warps_per_cta, 1));
     }
     return GG_OK;
 }
 
-// Enqueue one cooperative launch of `npasses` passes of T steps on stream st.
-int launch_passes(gg_batch* b, int T, int npasses, int parity0, cudaStream_t st)
+// Enqueue one cooperative launch of `npasses` passes of T steps on stream st
+// (variant 0: the plan's T; variant 1: T = 1).
+int launch_passes(gg_batch* b, int T, int variant, int npasses, int parity0, cudaStream_t st)
 {
-    const Plan32& p = b->plan;
-    const int sw = p.bx + 2 * p.halo;
-    size_t smem = 0;
-    BatchKernel k = kernel_for(b, T, &smem);
+    BatchKernel k = kernel_for(b, T);
     const int ctas = b->ctas_for_T[T];
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ctas);
-    cfg.blockDim = dim3(p.threads);
-    cfg.dynamicSmemBytes = smem;
+    cfg.blockDim = dim3(b->plan.threads);
+    cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -281,9 +278,9 @@ int launch_passes(gg_batch* b, int T, int npasses, int parity0, cudaStream_t st)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const unsigned expected = (unsigned)ctas + b->extra_arrivals;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k, (const InstDesc*)b->d_desc, (const int2*)b->d_items, b->nitems,
-                                       npasses, parity0, p.bx, p.by, p.halo, sw, b->d_bar, b->d_err, expected,
-                                       b->timeout_ns);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k, (const InstDesc*)b->d_desc, (const int2*)b->d_items[variant],
+                                       b->nitems[variant], npasses, parity0, variant, b->plan.by, b->d_bar,
+                                       b->d_err, expected, b->timeout_ns);
     if (e != cudaSuccess) return batch_fail(b, e, "batch launch");
     b->ctas = ctas;
     return GG_OK;
@@ -299,13 +296,13 @@ int enqueue_steps(gg_batch* b, int64_t nsteps, int parity, cudaStream_t st)
     int64_t left = main_passes;
     while (left > 0) {
         const int np = (int)std::min<int64_t>(left, 1 << 30);
-        int rc = launch_passes(b, T, np, par, st);
+        int rc = launch_passes(b, T, 0, np, par, st);
         if (rc != GG_OK) return rc;
         par = (par + np) & 1;
         left -= np;
     }
     if (rem) {
-        int rc = launch_passes(b, rem, 1, par, st);
+        int rc = launch_passes(b, 1, 1, rem, par, st);  // the remainder as single steps
         if (rc != GG_OK) return rc;
     }
     return GG_OK;
@@ -422,11 +419,13 @@ int gg_batch_create(int32_t n, const gg_grid* grids, const gg_params* params, co
     int maxnx = 0;
     for (auto& h : b->inst) maxnx = std::max(maxnx, h.nx);
     Plan32 plan;
+    plan.kind = 1;
     plan.T = params[0].steps_per_pass > 0 ? params[0].steps_per_pass : 1;
     plan.halo = plan.T;
-    plan.bx = std::min(round_up(maxnx, 4), 128);
+    plan.bx = 32 - 2 * plan.T;
     plan.by = 64;
     plan.threads = 128;
+    (void)maxnx;
     rc = configure(b, plan);
     if (rc != GG_OK) { gg_batch_destroy(b); return rc; }
     *out = b;
@@ -471,7 +470,7 @@ int gg_batch_step(gg_batch* b, int64_t nsteps)
         if (rc != GG_OK) return rc;
         b->captured = false;
     }
-    const int64_t passes = nsteps / b->plan.T + (nsteps % b->plan.T ? 1 : 0);
+    const int64_t passes = nsteps / b->plan.T + nsteps % b->plan.T;
     b->cur = (int)((b->cur + passes) & 1);
     b->steps += nsteps;
     return GG_OK;
@@ -485,7 +484,7 @@ int gg_batch_launch_info(const gg_batch* b, int32_t* info)
     info[2] = b->plan.by;
     info[3] = b->plan.threads;
     info[4] = b->ctas;
-    info[5] = b->nitems;
+    info[5] = b->nitems[0];
     info[6] = b->captured ? 1 : 0;
     return GG_OK;
 }
@@ -556,17 +555,15 @@ int gg_batch_autotune(gg_batch* b, int64_t trial_steps, int32_t* chosen)
     if (trial_steps < 1) trial_steps = 8;
     int maxnx = 0;
     for (auto& h : b->inst) maxnx = std::max(maxnx, h.nx);
-    // Candidates: strip width, chunk height, steps per pass.
+    // Candidates: steps per pass and chunk height of the warp tiles.
     std::vector<Plan32> cands;
-    for (int T : {1, 2, 4})
-        for (int bx : {128, 256})
-            for (int by : {32, 64, 128}) {
-                if (bx > round_up(maxnx, 4) && bx != 128) continue;
-                if (by < 8 * T) continue;
-                Plan32 p;
-                p.T = T; p.halo = T; p.bx = std::min(bx, round_up(maxnx, 4)); p.by = by; p.threads = 128;
-                cands.push_back(p);
-            }
+    for (int T = 1; T <= kBatchMaxT; ++T)
+        for (int by : {32, 64, 128}) {
+            if (by < 4 * T + 8) continue;
+            Plan32 p;
+            p.kind = 1; p.T = T; p.halo = T; p.bx = 32 - 2 * T; p.by = by; p.threads = 128;
+            cands.push_back(p);
+        }
     // Tuning runs advance the state: save it and restore it afterwards.
     const int nstate = b->kahan ? 6 : 3;
     size_t bytes = 0;
@@ -654,7 +651,8 @@ int gg_batch_destroy(gg_batch* b)
     cudaStreamSynchronize(b->stream);
     for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    if (b->d_items) cudaFree(b->d_items);
+    for (int v = 0; v < 2; ++v)
+        if (b->d_items[v]) cudaFree(b->d_items[v]);
     if (b->staging) cudaFree(b->staging);
     if (b->arena) cudaFree(b->arena);
     delete b;

@@ -81,6 +81,7 @@ _SIGNATURES = {
     "gg_adjoint": (ctypes.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _DP, _I64]),
     "gg_autotune": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(_I32)]),
     "gg_set_plan": (ctypes.c_int, [_VP, _I32, _I32, _I32, _I32]),
+    "gg_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
     "gg_dt": (ctypes.c_double, [_VP]),
     "gg_dt_max": (ctypes.c_double, [_VP]),
     "gg_step_count": (_I64, [_VP]),
@@ -277,6 +278,12 @@ class GGSim:
 
     def step(self, nsteps: int):
         _check(gg_step(self._sim, nsteps), self._sim, "gg_step")
+
+    def plan(self) -> Dict:
+        info = (_I32 * 4)()
+        _check(lib().gg_plan_info(self._sim, info), self._sim, "gg_plan_info")
+        kind = {0: "smem", 1: "warp", 2: "fp64"}[info[0]]
+        return dict(kind=kind, T=info[1], bx=info[2], by=info[3])
 
     def set_plan(self, kind: str = "warp", T: int = 1, strip: int = 0, chunk: int = 0):
         _check(lib().gg_set_plan(self._sim, 1 if kind == "warp" else 0, int(T), int(strip), int(chunk)),
