@@ -55,14 +55,22 @@ def parse():
 # ---------------------------------------------------------------- distributed plumbing
 
 class Dist:
-    def __init__(self, n):
+    """Rank bookkeeping from the torchrun environment.  NCCL when CUDA is
+    available, gloo otherwise; used only for the barrier and the max over
+    ranks of the timed region (no data-path collective)."""
+
+    def __init__(self, n=None, backend=None):
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         self.pg = None
+        self.device = "cpu"
         if self.world > 1:
+            import torch
             import torch.distributed as dist
-            backend = "nccl"
+            if backend is None:
+                backend = "nccl" if torch.cuda.is_available() else "gloo"
+            self.device = "cuda" if backend == "nccl" else "cpu"
             dist.init_process_group(backend)
             self.pg = dist
 
@@ -74,7 +82,7 @@ class Dist:
         if not self.pg:
             return x
         import torch
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
         self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
         return float(t.item())
 
@@ -149,8 +157,6 @@ def measured_peaks():
 # ---------------------------------------------------------------- reference arm (the oracle)
 
 def run_reference(args, dist):
-    if dist.rank != 0:
-        return
     import oracle
     from paper_2006_01748_gb300 import inputs
     oracle.build()
@@ -390,12 +396,17 @@ def run_ours(args, dist):
 
 def main():
     args = parse()
-    dist = Dist(args.gpus)
+    if args.impl == "reference":
+        # the oracle runs on rank 0 only; other ranks exit without work and
+        # without joining a process group
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        os.environ["WORLD_SIZE"] = "1"
+        run_reference(args, Dist())
+        return
+    dist = Dist()
     try:
-        if args.impl == "reference":
-            run_reference(args, dist)
-        else:
-            run_ours(args, dist)
+        run_ours(args, dist)
     finally:
         dist.close()
 

@@ -48,10 +48,9 @@ _lib = None
 _D = ctypes.POINTER(ctypes.c_double)
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build())
+def _configure(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    if True:
         P = ctypes.POINTER(_Problem)
         i64, i32, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         lib.ggo_coefficients.argtypes = [i64, _D, _D, _D, _D, _D, _D]
@@ -76,8 +75,21 @@ def _load():
         lib.ggo_adjoint.restype = ctypes.c_int
         lib.ggo_coefficients_vjp.argtypes = [i64, _D, _D, _D, _D, _D, _D, _D, _D, _D]
         lib.ggo_coefficients_vjp.restype = None
-        _lib = lib
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+def use_library(path: Optional[str]):
+    """Point the wrappers at another build of gg_oracle.c (None: the default
+    build).  Used by the tests that plant mistakes in a copy of the oracle."""
+    global _lib
+    _lib = None if path is None else _configure(ctypes.CDLL(path))
 
 
 def _p(a: np.ndarray):

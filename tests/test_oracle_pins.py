@@ -324,6 +324,8 @@ def test_diagnostics_definitions():
     U, V, W = inputs.random_state(nx, ny, 91)
     U[2, 3] = 0.001
     V[2, 3] = 0.002
+    U[0, 0], V[0, 0] = 0.003, 0.7   # only U below the gap threshold
+    U[1, 1], V[1, 1] = 0.6, 0.004   # only V below it
     W[4, 4] = np.nan
     d = oracle.diagnostics(U, V, W, 0.1, 0.2, eps=0.01)
     assert d["nonfinite"] == 1
@@ -332,6 +334,7 @@ def test_diagnostics_definitions():
     assert d["mass"][2] == pytest.approx(0.02 * np.nansum(W), rel=1e-14)
     assert d["tumour_area"] == pytest.approx(0.02 * (V > 0.5).sum())
     assert d["gap_area"] == pytest.approx(0.02 * ((U < 0.01) & (V < 0.01)).sum())
+    assert ((U < 0.01) & (V < 0.01)).sum() == 1
 
 
 # --------------------------------------------------------------- discrete adjoint
