@@ -39,12 +39,13 @@ using namespace gg;
 namespace {
 
 // Geometry of the warp-marching adjoint launch: 30 written columns per warp,
-// chunks of adj_chunk() rows sized for about 16 warps per SM (152 SMs).
+// chunks of adj_chunk() rows sized for about 20 warps per SM (152 SMs; the
+// kernel is bounded to 5 CTAs of 4 warps per SM).
 constexpr int kAdjOut = 30;
 inline int adj_strips(int nx) { return (nx + kAdjOut - 1) / kAdjOut; }
 inline int adj_chunk(int nx, int ny)
 {
-    const int chunks = std::max(1, (16 * 152 + adj_strips(nx) - 1) / adj_strips(nx));
+    const int chunks = std::max(1, (20 * 152 + adj_strips(nx) - 1) / adj_strips(nx));
     return std::min(128, std::max(8, (ny + chunks - 1) / chunks));
 }
 inline int adj_warps(int nx, int ny) { const int H = adj_chunk(nx, ny); return adj_strips(nx) * ((ny + H - 1) / H); }
@@ -73,8 +74,13 @@ __device__ __forceinline__ float from_west(float x) { return __shfl_up_sync(kFul
 __device__ __forceinline__ float from_east(float x) { return __shfl_down_sync(kFull, x, 1); }
 
 // One row of the inputs of an adjoint step at one column.
+// One row of the inputs of an adjoint step at one column: the fields read on
+// rows q-1, q, q+1 (Win) and those read on row q only (Own).
 struct AdjRow {
-    float u, v, w, lu, lv, lw, clu, clv, clw, a11, a12, a22, g11, g12, g22;
+    float u, v, w, lv, lw, clv, clw, a12, a22;
+};
+struct AdjOwn {
+    float lu, clu, a11, g11, g12, g22;
 };
 
 // Adjoint step as a warp march: the warp owns 32 columns (30 written) and a
@@ -93,21 +99,32 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
     const bool outc = ind && lane >= 1 && lane < 31;
     const int ys = chunk * H;
     const int ye = min(ny, ys + H);
+    // window fields two rows ahead, own-row fields one row ahead; each row of
+    // the gradient sums is read here before this warp writes it
     auto load = [&](int r, AdjRow& x) {
         if (ind && r >= 0 && r < ny) {
             const size_t o = (size_t)r * pitch + gx;
             x.u = __ldg(a.u + o); x.v = __ldg(a.v + o); x.w = __ldg(a.w + o);
-            x.lu = __ldg(a.lu + o); x.lv = __ldg(a.lv + o); x.lw = __ldg(a.lw + o);
+            x.lv = __ldg(a.lv + o); x.lw = __ldg(a.lw + o);
             if (KAHAN) {
-                x.clu = __ldg(a.clu + o); x.clv = __ldg(a.clv + o); x.clw = __ldg(a.clw + o);
+                x.clv = __ldg(a.clv + o); x.clw = __ldg(a.clw + o);
             } else {
-                x.clu = x.clv = x.clw = 0.0f;
+                x.clv = x.clw = 0.0f;
             }
-            x.a11 = __ldg(a.a11 + o); x.a12 = __ldg(a.a12 + o); x.a22 = __ldg(a.a22 + o);
-            x.g11 = a.g11[o]; x.g12 = a.g12[o]; x.g22 = a.g22[o];
+            x.a12 = __ldg(a.a12 + o); x.a22 = __ldg(a.a22 + o);
         } else {
-            x.u = x.v = x.w = x.lu = x.lv = x.lw = x.clu = x.clv = x.clw = 0.0f;
-            x.a11 = x.a12 = x.a22 = x.g11 = x.g12 = x.g22 = 0.0f;
+            x.u = x.v = x.w = x.lv = x.lw = x.clv = x.clw = x.a12 = x.a22 = 0.0f;
+        }
+    };
+    auto load_own = [&](int r, AdjOwn& x) {
+        if (ind && r >= 0 && r < ny) {
+            const size_t o = (size_t)r * pitch + gx;
+            x.lu = __ldg(a.lu + o);
+            x.clu = KAHAN ? __ldg(a.clu + o) : 0.0f;
+            x.a11 = __ldg(a.a11 + o);
+            x.g11 = __ldg(a.g11 + o); x.g12 = __ldg(a.g12 + o); x.g22 = __ldg(a.g22 + o);
+        } else {
+            x.lu = x.clu = x.a11 = x.g11 = x.g12 = x.g22 = 0.0f;
         }
     };
     // per-lane Kahan sums of the rate-gradient terms (delta, rho, D, c)
@@ -120,11 +137,17 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
     };
 
     AdjRow S, P, N, nxt;
+    AdjOwn PO, NO;
     load(ys - 1, S);
     load(ys, P);
     load(ys + 1, N);
     load(ys + 2, nxt);
+    load_own(ys, PO);
     for (int q = ys; q < ye; ++q) {
+        // issue the loads of rows q+3 (window) and q+1 (own fields) first
+        AdjRow nn;
+        load(q + 3, nn);
+        load_own(q + 1, NO);
         const bool hasS = q > 0, hasN = q + 1 < ny;
         // compensated difference of lamW between two (value, Kahan term) pairs
         auto dW = [](float la, float ca, float lb, float cb) { return __fsub_rn(__fsub_rn(la, lb), __fsub_rn(ca, cb)); };
@@ -147,10 +170,10 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
         float Tx;
         if (EDGE) Tx = (hasW ? SyW : 0.0f) - (hasE ? SyE : 0.0f) + SyP * ((hasE ? 0.0f : 1.0f) - (hasW ? 0.0f : 1.0f));
         else Tx = SyW - SyE;
-        float a11E = from_east(P.a11), a11W = from_west(P.a11);
-        if (EDGE) { if (!hasE) a11E = P.a11; if (!hasW) a11W = P.a11; }
+        float a11E = from_east(PO.a11), a11W = from_west(PO.a11);
+        if (EDGE) { if (!hasE) a11E = PO.a11; if (!hasW) a11W = PO.a11; }
         const float a22N = hasN ? N.a22 : P.a22, a22S = hasS ? S.a22 : P.a22;
-        const float D2T = ((P.a11 + a11E) * (-LxE_P) + (a11W + P.a11) * LxW_P) * k.kx +
+        const float D2T = ((PO.a11 + a11E) * (-LxE_P) + (a11W + PO.a11) * LxW_P) * k.kx +
                           ((P.a22 + a22N) * (-LyN) + (a22S + P.a22) * LyS) * k.ky + (Tx + Ty) * k.kc;
 
         // state and lamV neighbourhood (mirrored at the boundary)
@@ -179,39 +202,37 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
             fvv = k.D * d1T;
             fw = D2T;
         } else {
-            fu = (1.0f - 2.0f * P.u - k.delta * P.w) * P.lu + k.D * dU;
+            fu = (1.0f - 2.0f * P.u - k.delta * P.w) * PO.lu + k.D * dU;
             fvv = k.rho * (1.0f - 2.0f * P.v) * P.lv + k.D * d1T + k.c * P.lw;
-            fw = -k.delta * P.u * P.lu - k.c * P.lw + D2T;
+            fw = -k.delta * P.u * PO.lu - k.c * P.lw + D2T;
         }
-        // fetch the row after N while this row is finished
-        AdjRow nn;
-        load(q + 3, nn);
         if (outc) {
             const size_t o = (size_t)q * pitch + gx;
             if (!k.no_reaction) {
-                accum(0, -P.lu * P.u * P.w);
+                accum(0, -PO.lu * P.u * P.w);
                 accum(1, P.lv * P.v * (1.0f - P.v));
                 accum(3, P.lw * (P.v - P.w));
             }
             accum(2, P.lv * d1);
             if (KAHAN) {
                 float x, cx;
-                kahan_add(P.lu, k.dt * fu, P.clu, x, cx); a.luo[o] = x; a.cluo[o] = cx;
+                kahan_add(PO.lu, k.dt * fu, PO.clu, x, cx); a.luo[o] = x; a.cluo[o] = cx;
                 kahan_add(P.lv, k.dt * fvv, P.clv, x, cx); a.lvo[o] = x; a.clvo[o] = cx;
                 kahan_add(P.lw, k.dt * fw, P.clw, x, cx); a.lwo[o] = x; a.clwo[o] = cx;
             } else {
-                a.luo[o] = P.lu + k.dt * fu;
+                a.luo[o] = PO.lu + k.dt * fu;
                 a.lvo[o] = P.lv + k.dt * fvv;
                 a.lwo[o] = P.lw + k.dt * fw;
             }
-            a.g11[o] = P.g11 + k.dt * (((wE - P.w) * LxE_P + (P.w - wW) * LxW_P) * k.kx);
-            a.g22[o] = P.g22 + k.dt * (((wN - P.w) * LyN + (P.w - wS) * LyS) * k.ky);
-            a.g12[o] = P.g12 + k.dt * (((LxE_P + LxW_P) * (wN - wS) + (LyN + LyS) * (wE - wW)) * k.kc);
+            a.g11[o] = PO.g11 + k.dt * (((wE - P.w) * LxE_P + (P.w - wW) * LxW_P) * k.kx);
+            a.g22[o] = PO.g22 + k.dt * (((wN - P.w) * LyN + (P.w - wS) * LyS) * k.ky);
+            a.g12[o] = PO.g12 + k.dt * (((LxE_P + LxW_P) * (wN - wS) + (LyN + LyS) * (wE - wW)) * k.kc);
         }
         S = P;
         P = N;
         N = nxt;
         nxt = nn;
+        PO = NO;
     }
     // fold the per-lane sums into this warp's FP64 record (fixed order)
     double s4[4];
@@ -226,7 +247,7 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
 }
 
 template <bool KAHAN>
-__global__ void __launch_bounds__(128) adjoint_step_kernel(const AdjArgs a, const Rates32 k, const int H,
+__global__ void __launch_bounds__(128, 5) adjoint_step_kernel(const AdjArgs a, const Rates32 k, const int H,
                                                            const int nstrips, const int nwarps)
 {
     const int lane = threadIdx.x & 31;
@@ -388,8 +409,10 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
     if (e != cudaSuccess) return cuda_fail(s, e, "adjoint setup");
 
     const Rates32 r = rates32(s);
-    Plan32 plan1 = s->plan;
-    plan1.T = 1;
+    // recompute depth and chunk height: the simulation's warp plan when it has
+    // one, else single steps
+    const int TR = s->plan.kind == 1 ? s->plan.T : 1;
+    const int HR = s->plan.kind == 1 ? s->plan.by : default_plan(s->nx, s->ny, 1).by;
     const int aH = adj_chunk(s->nx, s->ny), astrips = adj_strips(s->nx), awarps = adj_warps(s->nx, s->ny);
     const int ablocks = (awarps + 3) / 4;
     int lb = 0;          // current lam buffer
@@ -406,21 +429,37 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
         auto state = [&](int kk, int f) -> float* {  // u, v, w of X^{seg*K + kk}
             return kk == 0 ? w->ckpt[(size_t)seg * nstate + f] : w->stash[(size_t)kk * 3 + f];
         };
-        auto comp = [&](int kk, int f) -> float* {
-            if (!kahan) return nullptr;
-            return kk == 0 ? w->ckpt[(size_t)seg * nstate + 3 + f] : w->scomp[kk & 1][f];
+        auto comp = [&](int kk, int f) -> float* {  // Kahan terms of the segment's first state
+            (void)kk;
+            return kahan ? w->ckpt[(size_t)seg * nstate + 3 + f] : nullptr;
         };
-        for (int kk = 0; kk + 1 < len && e == cudaSuccess; ++kk) {
+        // Recompute X^{seg K + 1 .. seg K + len - 1} in passes of up to TR steps;
+        // the intermediate levels of a pass write their states straight into
+        // the stash, the Kahan terms alternate between two buffers per pass.
+        int kk = 0, pass = 0;
+        while (kk + 1 < len && e == cudaSuccess) {
+            const int Tp = std::min(TR, len - 1 - kk);
             Grid32 g;
             g.u = state(kk, 0); g.v = state(kk, 1); g.w = state(kk, 2);
-            g.cu = comp(kk, 0); g.cv = comp(kk, 1); g.cw = comp(kk, 2);
-            g.uo = state(kk + 1, 0); g.vo = state(kk + 1, 1); g.wo = state(kk + 1, 2);
-            g.cuo = kahan ? w->scomp[(kk + 1) & 1][0] : nullptr;
-            g.cvo = kahan ? w->scomp[(kk + 1) & 1][1] : nullptr;
-            g.cwo = kahan ? w->scomp[(kk + 1) & 1][2] : nullptr;
+            const bool first = kk == 0;
+            g.cu = kahan ? (first ? comp(0, 0) : w->scomp[pass & 1][0]) : nullptr;
+            g.cv = kahan ? (first ? comp(0, 1) : w->scomp[pass & 1][1]) : nullptr;
+            g.cw = kahan ? (first ? comp(0, 2) : w->scomp[pass & 1][2]) : nullptr;
+            g.uo = state(kk + Tp, 0); g.vo = state(kk + Tp, 1); g.wo = state(kk + Tp, 2);
+            g.cuo = kahan ? w->scomp[(pass + 1) & 1][0] : nullptr;
+            g.cvo = kahan ? w->scomp[(pass + 1) & 1][1] : nullptr;
+            g.cwo = kahan ? w->scomp[(pass + 1) & 1][2] : nullptr;
             g.a11 = s->a32[0]; g.a12 = s->a32[1]; g.a22 = s->a32[2];
             g.nx = s->nx; g.ny = s->ny; g.pitch = s->pitch;
-            e = launch_plan(g, r, plan1, 1, kahan, st);
+            Stash32 sh = {};
+            for (int t = 1; t < Tp; ++t) {
+                sh.u[t - 1] = state(kk + t, 0);
+                sh.v[t - 1] = state(kk + t, 1);
+                sh.w[t - 1] = state(kk + t, 2);
+            }
+            e = launch_stepw_stash(g, r, HR, Tp, kahan, sh, st);
+            kk += Tp;
+            ++pass;
         }
         for (int kk = len - 1; kk >= 0 && e == cudaSuccess; --kk) {
             AdjArgs a;

@@ -47,6 +47,17 @@ struct Plan32 {
 
 size_t step32_smem_bytes(const Plan32& p, bool kahan);
 cudaError_t launch_stepw(const Grid32& g, const Rates32& r, int H, int T, bool kahan, cudaStream_t s);
+
+// Destinations of the intermediate time levels of a pass (level t = 1..T-1
+// writes u, v, w of step s0 + t to u[t-1], v[t-1], w[t-1]); used to
+// recompute every state of an adjoint segment in passes of T steps.
+struct Stash32 {
+    float* u[3];
+    float* v[3];
+    float* w[3];
+};
+cudaError_t launch_stepw_stash(const Grid32& g, const Rates32& r, int H, int T, bool kahan, const Stash32& st,
+                               cudaStream_t s);
 // One pass of T steps with the kernel the plan names.
 cudaError_t launch_plan(const Grid32& g, const Rates32& r, const Plan32& p, int T, bool kahan, cudaStream_t s);
 cudaError_t launch_step32(const Grid32& g, const Rates32& r, const Plan32& p, int T, bool kahan,

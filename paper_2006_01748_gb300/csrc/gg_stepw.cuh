@@ -39,9 +39,9 @@ __device__ __forceinline__ float ld_state(const float* p)
     else return __ldg(p);
 }
 
-template <int T, bool KAHAN, bool EDGE, bool COHERENT = false>
+template <int T, bool KAHAN, bool EDGE, bool COHERENT = false, bool STASH = false>
 __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, const int H, const int strip,
-                                          const int chunk, const int lane)
+                                          const int chunk, const int lane, const Stash32* stash = nullptr)
 {
     constexpr int OUT = 32 - 2 * T;
     const int nx = g.nx, ny = g.ny, pitch = g.pitch;
@@ -171,6 +171,16 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
                     }
                 }
             } else {
+                if constexpr (STASH) {
+                    // intermediate level: also write the own rows and columns of step s0 + t
+                    if (q >= ys && q < hiT && outc) {
+                        const size_t o = (size_t)q * pitch + gx;
+                        const int li = (t < T) ? t - 1 : 0;
+                        stash->u[li][o] = un;
+                        stash->v[li][o] = vn;
+                        stash->w[li][o] = wn;
+                    }
+                }
                 const int tt = (t < T) ? t : 0;  // level t passes row q on
                 sW[tt] = pW[tt]; pU[tt] = nU[tt]; pV[tt] = nV[tt]; pW[tt] = nW[tt];
                 nU[tt] = un; nV[tt] = vn; nW[tt] = wn;
