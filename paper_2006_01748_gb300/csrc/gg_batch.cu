@@ -89,7 +89,6 @@ __global__ void __launch_bounds__(128) batch_kernel(const InstDesc* __restrict__
     if (threadIdx.x == 0) s_gen = atomicAdd(&bar[1], 0u);
     __syncthreads();
     unsigned gen = s_gen;
-    constexpr int OUT = 32 - 2 * T;
     const int lane = threadIdx.x & 31;
     const int wpc = blockDim.x >> 5;
     for (int pass = 0; pass < npasses; ++pass) {
@@ -99,11 +98,7 @@ __global__ void __launch_bounds__(128) batch_kernel(const InstDesc* __restrict__
             const InstDesc& d = desc[it.x];
             const int strips = d.strips[variant];
             const int sx = it.y % strips, sy = it.y / strips;
-            const int gx0 = sx * OUT - T;
-            if (gx0 >= 1 && gx0 + 31 <= d.g[parity].nx - 2)
-                stepw::warp_pass<T, KAHAN, false, true>(d.g[parity], d.r, H, sx, sy, lane);
-            else
-                stepw::warp_pass<T, KAHAN, true, true>(d.g[parity], d.r, H, sx, sy, lane);
+            stepw::warp_pass_any<T, KAHAN, true>(d.g[parity], d.r, H, sx, sy, lane);
         }
         if (pass + 1 < npasses && !grid_barrier(bar, err, expected, gen, timeout_ns, &s_ok)) return;
     }

@@ -11,13 +11,8 @@ __global__ void __launch_bounds__(128) stepw_kernel(const Grid32 g, const Rates3
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw >= nwarps) return;  // whole warps only
-    constexpr int OUT = 32 - 2 * T;
     const int strip = gw % nstrips, chunk = gw / nstrips;
-    const int gx0 = strip * OUT - T;
-    if (gx0 >= 1 && gx0 + 31 <= g.nx - 2)
-        stepw::warp_pass<T, KAHAN, false>(g, k, H, strip, chunk, lane);
-    else
-        stepw::warp_pass<T, KAHAN, true>(g, k, H, strip, chunk, lane);
+    stepw::warp_pass_any<T, KAHAN>(g, k, H, strip, chunk, lane);
 }
 
 template <int T, bool KAHAN>
@@ -27,13 +22,8 @@ __global__ void __launch_bounds__(128) stepw_stash_kernel(const Grid32 g, const 
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw >= nwarps) return;
-    constexpr int OUT = 32 - 2 * T;
     const int strip = gw % nstrips, chunk = gw / nstrips;
-    const int gx0 = strip * OUT - T;
-    if (gx0 >= 1 && gx0 + 31 <= g.nx - 2)
-        stepw::warp_pass<T, KAHAN, false, false, true>(g, k, H, strip, chunk, lane, &st);
-    else
-        stepw::warp_pass<T, KAHAN, true, false, true>(g, k, H, strip, chunk, lane, &st);
+    stepw::warp_pass_any<T, KAHAN, false, true>(g, k, H, strip, chunk, lane, &st);
 }
 
 template <int T, bool KAHAN>

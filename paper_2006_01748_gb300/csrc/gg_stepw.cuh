@@ -39,7 +39,10 @@ __device__ __forceinline__ float ld_state(const float* p)
     else return __ldg(p);
 }
 
-template <int T, bool KAHAN, bool EDGE, bool COHERENT = false, bool STASH = false>
+// EDGE: the strip touches the west or east domain boundary.  YEDGE: the
+// chunk's rows (with their halo of T rows) touch the south or north boundary;
+// interior chunks take every south / north face as present.
+template <int T, bool KAHAN, bool EDGE, bool COHERENT = false, bool STASH = false, bool YEDGE = true>
 __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, const int H, const int strip,
                                           const int chunk, const int lane, const Stash32* stash = nullptr)
 {
@@ -118,7 +121,7 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
         for (int t = 1; t <= T; ++t) {
             const int q = R - t;
             const bool valid = q >= max(0, ys - T + t) && q < min(ny, ys + H + T - t);  // warp-uniform
-            const bool hasS = q > 0, hasN = q + 1 < ny;
+            const bool hasS = YEDGE ? q > 0 : true, hasN = YEDGE ? q + 1 < ny : true;
             const float uP = pU[t - 1], vP = pV[t - 1], wP = pW[t - 1];
             const float uN = nU[t - 1], vN = nV[t - 1], wN = nW[t - 1];
             const float a11P = cf[t][0], bP = cf[t][1], a22P = cf[t][2];
@@ -198,6 +201,26 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
     for (int tk = 0; tk < nticks; tk += 2) {
         tick(tk, inA);
         if (tk + 1 < nticks) tick(tk + 1, inB);
+    }
+}
+
+// Runs warp_pass with the variant that matches the warp's position: interior
+// strips skip the east / west boundary handling, interior chunks the south /
+// north one.
+template <int T, bool KAHAN, bool COHERENT = false, bool STASH = false>
+__device__ __forceinline__ void warp_pass_any(const Grid32& g, const Rates32& k, const int H, const int strip,
+                                              const int chunk, const int lane, const Stash32* stash = nullptr)
+{
+    constexpr int OUT = 32 - 2 * T;
+    const int gx0 = strip * OUT - T;
+    const bool xin = gx0 >= 1 && gx0 + 31 <= g.nx - 2;
+    const int ys = chunk * H;
+    const bool yin = ys - T >= 1 && ys + H + T <= g.ny - 1;
+    if (xin) {
+        if (yin) warp_pass<T, KAHAN, false, COHERENT, STASH, false>(g, k, H, strip, chunk, lane, stash);
+        else warp_pass<T, KAHAN, false, COHERENT, STASH, true>(g, k, H, strip, chunk, lane, stash);
+    } else {
+        warp_pass<T, KAHAN, true, COHERENT, STASH, true>(g, k, H, strip, chunk, lane, stash);
     }
 }
 
