@@ -165,14 +165,24 @@ int gg_diagnostics_eps(gg_sim* sim, double eps, gg_diag* out);
  *   g_scalars: host, 4 doubles: dL/d(delta, rho, D, c); may be NULL.
  *   checkpoint_every: steps between stored states (0 = about sqrt(nsteps)).
  * The forward pass is recomputed from stored checkpoints segment by segment
- * (sqrt(N) checkpointing).  On return the simulation holds the state at step
- * nsteps, as after gg_step(sim, nsteps).  Not available for GG_FP64_PLAIN
+ * (sqrt(N) checkpointing); the states of the last segments, as many as fit
+ * in 60 % of (this workspace's kept-state buffer + the free device memory),
+ * are kept from the forward pass instead of recomputed.  The workspace
+ * (checkpoints, recompute stash, kept states, adjoint fields) is allocated by
+ * the first call, reused by later calls and freed by gg_adjoint_release or
+ * gg_destroy.  On return the simulation holds the state at step nsteps, as
+ * after gg_step(sim, nsteps).  Not available for GG_FP64_PLAIN
  * (GG_ERR_STATE).  Synchronizes. */
 int gg_adjoint(gg_sim* sim, int64_t nsteps,
                const float* dLdu_N, const float* dLdv_N, const float* dLdw_N,
                float* g_theta, float* g_lambda1, float* g_lambda2,
                float* g_u0, float* g_v0, float* g_w0,
                double* g_scalars, int64_t checkpoint_every);
+
+/* Frees the adjoint workspace of sim (a no-op when it has none); the next
+ * gg_adjoint allocates it again.  The simulation's state is untouched.
+ * Returns GG_OK, or GG_ERR_ARG for a NULL sim.  Synchronizes the device. */
+int gg_adjoint_release(gg_sim* sim);
 
 /* Diagnostics without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- code

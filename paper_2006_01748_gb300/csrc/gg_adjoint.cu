@@ -49,7 +49,15 @@ inline int adj_chunk(int nx, int ny)
     return std::min(128, std::max(8, (ny + chunks - 1) / chunks));
 }
 inline int adj_warps(int nx, int ny) { const int H = adj_chunk(nx, ny); return adj_strips(nx) * ((ny + H - 1) / H); }
-constexpr int kFlushEvery = 16;  // FP32 per-cell gradient sums are folded into FP64 this often
+// The two-step kernel writes 28 columns per warp and runs 4 CTAs per SM.
+inline int adj2_strips(int nx) { return (nx + 27) / 28; }
+inline int adj2_chunk(int nx, int ny)
+{
+    const int chunks = std::max(1, (16 * 152 + adj2_strips(nx) - 1) / adj2_strips(nx));
+    return std::min(128, std::max(8, (ny + chunks - 1) / chunks));
+}
+inline int adj2_warps(int nx, int ny) { const int H = adj2_chunk(nx, ny); return adj2_strips(nx) * ((ny + H - 1) / H); }
+constexpr int kFlushEvery = 32;  // FP32 per-cell gradient sums are folded into FP64 this often
 
 struct AdjArgs {
     const float *u, *v, *w;                          // X^k
@@ -73,22 +81,165 @@ constexpr unsigned kFull = 0xffffffffu;
 __device__ __forceinline__ float from_west(float x) { return __shfl_up_sync(kFull, x, 1); }
 __device__ __forceinline__ float from_east(float x) { return __shfl_down_sync(kFull, x, 1); }
 
-// One row of the inputs of an adjoint step at one column.
 // One row of the inputs of an adjoint step at one column: the fields read on
-// rows q-1, q, q+1 (Win) and those read on row q only (Own).
+// rows q-1, q, q+1 (AdjRow) and those read on row q only (AdjOwn).
 struct AdjRow {
     float u, v, w, lv, lw, clv, clw, a12, a22;
 };
 struct AdjOwn {
     float lu, clu, a11, g11, g12, g22;
 };
+// Result of one adjoint level at one cell: lam at step k with its Kahan
+// terms, dt times the tensor-gradient increments, the four rate terms.
+struct AdjOut {
+    float lu, clu, lv, clv, lw, clw;
+    float d11, d12, d22;
+    float s_delta, s_rho, s_D, s_c;
+};
+
+// One adjoint step at row q of one lane, from the rows S (q-1), P (q), N (q+1)
+// of lam^{k+1} and X^k and the own-row fields lu, clu, a11.  All lanes of the
+// warp call it (it shuffles).
+template <bool KAHAN, bool EDGE, bool YEDGE = true>
+__device__ __forceinline__ AdjOut adj_level(const Rates32& k, const AdjRow& S, const AdjRow& P, const AdjRow& N,
+                                            float lu, float clu, float a11, bool hasW, bool hasE, bool hasS_,
+                                            bool hasN_)
+{
+    // interior chunks (YEDGE false) have both the south and the north face
+    const bool hasS = YEDGE ? hasS_ : true, hasN = YEDGE ? hasN_ : true;
+    // compensated difference of lam between two (value, Kahan term) pairs
+    auto dW = [](float la, float ca, float lb, float cb) { return __fsub_rn(__fsub_rn(la, lb), __fsub_rn(ca, cb)); };
+    // face differences of lamW on rows S, P, N (0 on boundary faces)
+    auto lx_e = [&](const AdjRow& X) {
+        float le = from_east(X.lw), ce = from_east(X.clw);
+        const float d = dW(X.lw, X.clw, le, ce);
+        return hasE ? d : 0.0f;
+    };
+    const float LxE_P = lx_e(P), LxE_N = lx_e(N), LxE_S = lx_e(S);
+    float LxW_P = from_west(LxE_P), LxW_N = from_west(LxE_N), LxW_S = from_west(LxE_S);
+    if (EDGE && !hasW) { LxW_P = LxW_N = LxW_S = 0.0f; }
+    const float LyN = hasN ? dW(P.lw, P.clw, N.lw, N.clw) : 0.0f;
+    const float LyS = hasS ? dW(S.lw, S.clw, P.lw, P.clw) : 0.0f;
+    // transpose of the a12 cross terms (mirrored central differences)
+    const float SxP = P.a12 * (LxE_P + LxW_P), SxN = N.a12 * (LxE_N + LxW_N), SxS = S.a12 * (LxE_S + LxW_S);
+    const float SyP = P.a12 * (LyN + LyS);
+    float SyE = from_east(SyP), SyW = from_west(SyP);
+    const float Ty = (hasS ? SxS : 0.0f) - (hasN ? SxN : 0.0f) + SxP * ((hasN ? 0.0f : 1.0f) - (hasS ? 0.0f : 1.0f));
+    float Tx;
+    if (EDGE) Tx = (hasW ? SyW : 0.0f) - (hasE ? SyE : 0.0f) + SyP * ((hasE ? 0.0f : 1.0f) - (hasW ? 0.0f : 1.0f));
+    else Tx = SyW - SyE;
+    float a11E = from_east(a11), a11W = from_west(a11);
+    if (EDGE) { if (!hasE) a11E = a11; if (!hasW) a11W = a11; }
+    const float a22N = hasN ? N.a22 : P.a22, a22S = hasS ? S.a22 : P.a22;
+    const float D2T = ((a11 + a11E) * (-LxE_P) + (a11W + a11) * LxW_P) * k.kx +
+                      ((P.a22 + a22N) * (-LyN) + (a22S + P.a22) * LyS) * k.ky + (Tx + Ty) * k.kc;
+
+    // state and lamV neighbourhood (mirrored at the boundary)
+    float uE = from_east(P.u), uW = from_west(P.u), vE = from_east(P.v), vW = from_west(P.v);
+    float wE = from_east(P.w), wW = from_west(P.w);
+    float lvE = from_east(P.lv), lvW = from_west(P.lv), cvE = from_east(P.clv), cvW = from_west(P.clv);
+    if (EDGE) {
+        if (!hasE) { uE = P.u; vE = P.v; wE = P.w; lvE = P.lv; cvE = P.clv; }
+        if (!hasW) { uW = P.u; vW = P.v; wW = P.w; lvW = P.lv; cvW = P.clv; }
+    }
+    const float uN = hasN ? N.u : P.u, uS = hasS ? S.u : P.u;
+    const float vN = hasN ? N.v : P.v, vS = hasS ? S.v : P.v;
+    const float wN = hasN ? N.w : P.w, wS = hasS ? S.w : P.w;
+    const float dlE = dW(lvE, cvE, P.lv, P.clv), dlW = dW(lvW, cvW, P.lv, P.clv);
+    const float dlN = hasN ? dW(N.lv, N.clv, P.lv, P.clv) : 0.0f, dlS = hasS ? dW(S.lv, S.clv, P.lv, P.clv) : 0.0f;
+    const float mE = 1.0f - 0.5f * (P.u + uE), mW = 1.0f - 0.5f * (P.u + uW);
+    const float mN = 1.0f - 0.5f * (P.u + uN), mS = 1.0f - 0.5f * (P.u + uS);
+    const float dvE = vE - P.v, dvW = vW - P.v, dvN = vN - P.v, dvS = vS - P.v;
+    const float d1 = (mE * dvE + mW * dvW) * k.ihx2 + (mN * dvN + mS * dvS) * k.ihy2;
+    const float d1T = (mE * dlE + mW * dlW) * k.ihx2 + (mN * dlN + mS * dlS) * k.ihy2;
+    const float dU = 0.5f * ((dvE * dlE + dvW * dlW) * k.ihx2 + (dvN * dlN + dvS * dlS) * k.ihy2);
+
+    float fu, fvv, fw;
+    AdjOut o;
+    if (k.no_reaction) {
+        fu = k.D * dU;
+        fvv = k.D * d1T;
+        fw = D2T;
+        o.s_delta = o.s_rho = o.s_c = 0.0f;
+    } else {
+        fu = (1.0f - 2.0f * P.u - k.delta * P.w) * lu + k.D * dU;
+        fvv = k.rho * (1.0f - 2.0f * P.v) * P.lv + k.D * d1T + k.c * P.lw;
+        fw = -k.delta * P.u * lu - k.c * P.lw + D2T;
+        o.s_delta = -lu * P.u * P.w;
+        o.s_rho = P.lv * P.v * (1.0f - P.v);
+        o.s_c = P.lw * (P.v - P.w);
+    }
+    o.s_D = P.lv * d1;
+    if (KAHAN) {
+        kahan_add(lu, k.dt * fu, clu, o.lu, o.clu);
+        kahan_add(P.lv, k.dt * fvv, P.clv, o.lv, o.clv);
+        kahan_add(P.lw, k.dt * fw, P.clw, o.lw, o.clw);
+    } else {
+        o.lu = lu + k.dt * fu;
+        o.lv = P.lv + k.dt * fvv;
+        o.lw = P.lw + k.dt * fw;
+        o.clu = o.clv = o.clw = 0.0f;
+    }
+    o.d11 = k.dt * (((wE - P.w) * LxE_P + (P.w - wW) * LxW_P) * k.kx);
+    o.d22 = k.dt * (((wN - P.w) * LyN + (P.w - wS) * LyS) * k.ky);
+    o.d12 = k.dt * (((LxE_P + LxW_P) * (wN - wS) + (LyN + LyS) * (wE - wW)) * k.kc);
+    return o;
+}
+
+// Per-lane FP32 Kahan sums of the four rate terms, folded into one FP64
+// record per warp at the end of the chunk (fixed order).
+struct RateSums {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f}, accc[4] = {0.f, 0.f, 0.f, 0.f};
+    __device__ __forceinline__ void add(int q, float x)
+    {
+        const float y = __fsub_rn(x, accc[q]);
+        const float t = __fadd_rn(acc[q], y);
+        accc[q] = __fsub_rn(__fsub_rn(t, acc[q]), y);
+        acc[q] = t;
+    }
+    __device__ __forceinline__ void add_all(const AdjOut& o)
+    {
+        add(0, o.s_delta);
+        add(1, o.s_rho);
+        add(2, o.s_D);
+        add(3, o.s_c);
+    }
+    __device__ __forceinline__ void fold(double* part, int lane, float dt)
+    {
+        double s4[4];
+        for (int qq = 0; qq < 4; ++qq) {
+            s4[qq] = (double)acc[qq] - (double)accc[qq];
+            for (int off = 16; off > 0; off >>= 1) s4[qq] += __shfl_xor_sync(kFull, s4[qq], off);
+        }
+        if (lane == 0) {
+            const double dtd = (double)dt;
+            for (int qq = 0; qq < 4; ++qq) part[qq] += dtd * s4[qq];
+        }
+    }
+};
+
+// Loads of one row at one column (zeros outside the domain).
+template <bool KAHAN>
+__device__ __forceinline__ void load_row(const float* u, const float* v, const float* w, const float* lv,
+                                         const float* lw, const float* clv, const float* clw, const float* a12,
+                                         const float* a22, bool in, size_t o, AdjRow& x)
+{
+    if (in) {
+        x.u = __ldg(u + o); x.v = __ldg(v + o); x.w = __ldg(w + o);
+        x.lv = __ldg(lv + o); x.lw = __ldg(lw + o);
+        if (KAHAN) { x.clv = __ldg(clv + o); x.clw = __ldg(clw + o); }
+        else { x.clv = x.clw = 0.0f; }
+        x.a12 = __ldg(a12 + o); x.a22 = __ldg(a22 + o);
+    } else {
+        x.u = x.v = x.w = x.lv = x.lw = x.clv = x.clw = x.a12 = x.a22 = 0.0f;
+    }
+}
 
 // Adjoint step as a warp march: the warp owns 32 columns (30 written) and a
-// chunk of H rows, keeps rows q-1, q, q+1 of its inputs in registers (the
-// next row is fetched one row ahead) and takes east / west values by
-// shuffle.  The four rate gradients are summed per lane with FP32 Kahan sums
-// and folded into one FP64 record per warp at the end of the chunk.
-template <bool KAHAN, bool EDGE>
+// chunk of H rows, keeps rows q-1, q, q+1 of its inputs in registers (window
+// rows fetched two ahead, own-row fields one ahead) and takes east / west
+// values by shuffle.
+template <bool KAHAN, bool EDGE, bool YEDGE>
 __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, const int H, const int strip,
                                          const int chunk, const int lane, double* part)
 {
@@ -99,22 +250,9 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
     const bool outc = ind && lane >= 1 && lane < 31;
     const int ys = chunk * H;
     const int ye = min(ny, ys + H);
-    // window fields two rows ahead, own-row fields one row ahead; each row of
-    // the gradient sums is read here before this warp writes it
     auto load = [&](int r, AdjRow& x) {
-        if (ind && r >= 0 && r < ny) {
-            const size_t o = (size_t)r * pitch + gx;
-            x.u = __ldg(a.u + o); x.v = __ldg(a.v + o); x.w = __ldg(a.w + o);
-            x.lv = __ldg(a.lv + o); x.lw = __ldg(a.lw + o);
-            if (KAHAN) {
-                x.clv = __ldg(a.clv + o); x.clw = __ldg(a.clw + o);
-            } else {
-                x.clv = x.clw = 0.0f;
-            }
-            x.a12 = __ldg(a.a12 + o); x.a22 = __ldg(a.a22 + o);
-        } else {
-            x.u = x.v = x.w = x.lv = x.lw = x.clv = x.clw = x.a12 = x.a22 = 0.0f;
-        }
+        load_row<KAHAN>(a.u, a.v, a.w, a.lv, a.lw, a.clv, a.clw, a.a12, a.a22, ind && r >= 0 && r < ny,
+                        (size_t)r * pitch + gx, x);
     };
     auto load_own = [&](int r, AdjOwn& x) {
         if (ind && r >= 0 && r < ny) {
@@ -127,15 +265,7 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
             x.lu = x.clu = x.a11 = x.g11 = x.g12 = x.g22 = 0.0f;
         }
     };
-    // per-lane Kahan sums of the rate-gradient terms (delta, rho, D, c)
-    float acc[4] = {0.f, 0.f, 0.f, 0.f}, accc[4] = {0.f, 0.f, 0.f, 0.f};
-    auto accum = [&](int q, float x) {
-        const float y = __fsub_rn(x, accc[q]);
-        const float t = __fadd_rn(acc[q], y);
-        accc[q] = __fsub_rn(__fsub_rn(t, acc[q]), y);
-        acc[q] = t;
-    };
-
+    RateSums sums;
     AdjRow S, P, N, nxt;
     AdjOwn PO, NO;
     load(ys - 1, S);
@@ -144,89 +274,19 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
     load(ys + 2, nxt);
     load_own(ys, PO);
     for (int q = ys; q < ye; ++q) {
-        // issue the loads of rows q+3 (window) and q+1 (own fields) first
         AdjRow nn;
         load(q + 3, nn);
         load_own(q + 1, NO);
-        const bool hasS = q > 0, hasN = q + 1 < ny;
-        // compensated difference of lamW between two (value, Kahan term) pairs
-        auto dW = [](float la, float ca, float lb, float cb) { return __fsub_rn(__fsub_rn(la, lb), __fsub_rn(ca, cb)); };
-        // face differences of lamW on rows S, P, N (0 on boundary faces)
-        auto lx_e = [&](const AdjRow& X) {
-            float le = from_east(X.lw), ce = from_east(X.clw);
-            const float d = dW(X.lw, X.clw, le, ce);
-            return hasE ? d : 0.0f;
-        };
-        const float LxE_P = lx_e(P), LxE_N = lx_e(N), LxE_S = lx_e(S);
-        float LxW_P = from_west(LxE_P), LxW_N = from_west(LxE_N), LxW_S = from_west(LxE_S);
-        if (EDGE && !hasW) { LxW_P = LxW_N = LxW_S = 0.0f; }
-        const float LyN = hasN ? dW(P.lw, P.clw, N.lw, N.clw) : 0.0f;
-        const float LyS = hasS ? dW(S.lw, S.clw, P.lw, P.clw) : 0.0f;
-        // transpose of the a12 cross terms (mirrored central differences)
-        const float SxP = P.a12 * (LxE_P + LxW_P), SxN = N.a12 * (LxE_N + LxW_N), SxS = S.a12 * (LxE_S + LxW_S);
-        const float SyP = P.a12 * (LyN + LyS);
-        float SyE = from_east(SyP), SyW = from_west(SyP);
-        const float Ty = (hasS ? SxS : 0.0f) - (hasN ? SxN : 0.0f) + SxP * ((hasN ? 0.0f : 1.0f) - (hasS ? 0.0f : 1.0f));
-        float Tx;
-        if (EDGE) Tx = (hasW ? SyW : 0.0f) - (hasE ? SyE : 0.0f) + SyP * ((hasE ? 0.0f : 1.0f) - (hasW ? 0.0f : 1.0f));
-        else Tx = SyW - SyE;
-        float a11E = from_east(PO.a11), a11W = from_west(PO.a11);
-        if (EDGE) { if (!hasE) a11E = PO.a11; if (!hasW) a11W = PO.a11; }
-        const float a22N = hasN ? N.a22 : P.a22, a22S = hasS ? S.a22 : P.a22;
-        const float D2T = ((PO.a11 + a11E) * (-LxE_P) + (a11W + PO.a11) * LxW_P) * k.kx +
-                          ((P.a22 + a22N) * (-LyN) + (a22S + P.a22) * LyS) * k.ky + (Tx + Ty) * k.kc;
-
-        // state and lamV neighbourhood (mirrored at the boundary)
-        float uE = from_east(P.u), uW = from_west(P.u), vE = from_east(P.v), vW = from_west(P.v);
-        float wE = from_east(P.w), wW = from_west(P.w);
-        float lvE = from_east(P.lv), lvW = from_west(P.lv), cvE = from_east(P.clv), cvW = from_west(P.clv);
-        if (EDGE) {
-            if (!hasE) { uE = P.u; vE = P.v; wE = P.w; lvE = P.lv; cvE = P.clv; }
-            if (!hasW) { uW = P.u; vW = P.v; wW = P.w; lvW = P.lv; cvW = P.clv; }
-        }
-        const float uN = hasN ? N.u : P.u, uS = hasS ? S.u : P.u;
-        const float vN = hasN ? N.v : P.v, vS = hasS ? S.v : P.v;
-        const float wN = hasN ? N.w : P.w, wS = hasS ? S.w : P.w;
-        const float dlE = dW(lvE, cvE, P.lv, P.clv), dlW = dW(lvW, cvW, P.lv, P.clv);
-        const float dlN = hasN ? dW(N.lv, N.clv, P.lv, P.clv) : 0.0f, dlS = hasS ? dW(S.lv, S.clv, P.lv, P.clv) : 0.0f;
-        const float mE = 1.0f - 0.5f * (P.u + uE), mW = 1.0f - 0.5f * (P.u + uW);
-        const float mN = 1.0f - 0.5f * (P.u + uN), mS = 1.0f - 0.5f * (P.u + uS);
-        const float dvE = vE - P.v, dvW = vW - P.v, dvN = vN - P.v, dvS = vS - P.v;
-        const float d1 = (mE * dvE + mW * dvW) * k.ihx2 + (mN * dvN + mS * dvS) * k.ihy2;
-        const float d1T = (mE * dlE + mW * dlW) * k.ihx2 + (mN * dlN + mS * dlS) * k.ihy2;
-        const float dU = 0.5f * ((dvE * dlE + dvW * dlW) * k.ihx2 + (dvN * dlN + dvS * dlS) * k.ihy2);
-
-        float fu, fvv, fw;
-        if (k.no_reaction) {
-            fu = k.D * dU;
-            fvv = k.D * d1T;
-            fw = D2T;
-        } else {
-            fu = (1.0f - 2.0f * P.u - k.delta * P.w) * PO.lu + k.D * dU;
-            fvv = k.rho * (1.0f - 2.0f * P.v) * P.lv + k.D * d1T + k.c * P.lw;
-            fw = -k.delta * P.u * PO.lu - k.c * P.lw + D2T;
-        }
+        const AdjOut o = adj_level<KAHAN, EDGE, YEDGE>(k, S, P, N, PO.lu, PO.clu, PO.a11, hasW, hasE, q > 0,
+                                                       q + 1 < ny);
         if (outc) {
-            const size_t o = (size_t)q * pitch + gx;
-            if (!k.no_reaction) {
-                accum(0, -PO.lu * P.u * P.w);
-                accum(1, P.lv * P.v * (1.0f - P.v));
-                accum(3, P.lw * (P.v - P.w));
-            }
-            accum(2, P.lv * d1);
-            if (KAHAN) {
-                float x, cx;
-                kahan_add(PO.lu, k.dt * fu, PO.clu, x, cx); a.luo[o] = x; a.cluo[o] = cx;
-                kahan_add(P.lv, k.dt * fvv, P.clv, x, cx); a.lvo[o] = x; a.clvo[o] = cx;
-                kahan_add(P.lw, k.dt * fw, P.clw, x, cx); a.lwo[o] = x; a.clwo[o] = cx;
-            } else {
-                a.luo[o] = PO.lu + k.dt * fu;
-                a.lvo[o] = P.lv + k.dt * fvv;
-                a.lwo[o] = P.lw + k.dt * fw;
-            }
-            a.g11[o] = PO.g11 + k.dt * (((wE - P.w) * LxE_P + (P.w - wW) * LxW_P) * k.kx);
-            a.g22[o] = PO.g22 + k.dt * (((wN - P.w) * LyN + (P.w - wS) * LyS) * k.ky);
-            a.g12[o] = PO.g12 + k.dt * (((LxE_P + LxW_P) * (wN - wS) + (LyN + LyS) * (wE - wW)) * k.kc);
+            const size_t off = (size_t)q * pitch + gx;
+            sums.add_all(o);
+            a.luo[off] = o.lu; a.lvo[off] = o.lv; a.lwo[off] = o.lw;
+            if (KAHAN) { a.cluo[off] = o.clu; a.clvo[off] = o.clv; a.clwo[off] = o.clw; }
+            a.g11[off] = PO.g11 + o.d11;
+            a.g12[off] = PO.g12 + o.d12;
+            a.g22[off] = PO.g22 + o.d22;
         }
         S = P;
         P = N;
@@ -234,21 +294,12 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
         nxt = nn;
         PO = NO;
     }
-    // fold the per-lane sums into this warp's FP64 record (fixed order)
-    double s4[4];
-    for (int qq = 0; qq < 4; ++qq) {
-        s4[qq] = (double)acc[qq] - (double)accc[qq];
-        for (int off = 16; off > 0; off >>= 1) s4[qq] += __shfl_xor_sync(kFull, s4[qq], off);
-    }
-    if (lane == 0) {
-        const double dtd = (double)k.dt;
-        for (int qq = 0; qq < 4; ++qq) part[qq] += dtd * s4[qq];
-    }
+    sums.fold(part, lane, k.dt);
 }
 
 template <bool KAHAN>
 __global__ void __launch_bounds__(128, 5) adjoint_step_kernel(const AdjArgs a, const Rates32 k, const int H,
-                                                           const int nstrips, const int nwarps)
+                                                              const int nstrips, const int nwarps)
 {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -256,8 +307,148 @@ __global__ void __launch_bounds__(128, 5) adjoint_step_kernel(const AdjArgs a, c
     const int strip = gw % nstrips, chunk = gw / nstrips;
     const int gx0 = strip * 30 - 1;
     double* part = a.partials + (size_t)gw * 4;
-    if (gx0 >= 1 && gx0 + 31 <= a.nx - 2) adj_warp<KAHAN, false>(a, k, H, strip, chunk, lane, part);
-    else adj_warp<KAHAN, true>(a, k, H, strip, chunk, lane, part);
+    const int ys = chunk * H;
+    const bool yin = ys - 1 >= 1 && ys + H + 1 <= a.ny - 1;
+    if (gx0 >= 1 && gx0 + 31 <= a.nx - 2) {
+        if (yin) adj_warp<KAHAN, false, false>(a, k, H, strip, chunk, lane, part);
+        else adj_warp<KAHAN, false, true>(a, k, H, strip, chunk, lane, part);
+    } else {
+        adj_warp<KAHAN, true, true>(a, k, H, strip, chunk, lane, part);
+    }
+}
+
+// Two adjoint steps per pass (steps k+1 and k of the reverse sweep).  Level 1
+// turns lam^{k+2} into lam^{k+1} with X^{k+1}; level 2 turns lam^{k+1} into
+// lam^k with X^k one row behind, so lam^{k+1} never leaves registers and the
+// per-cell gradient sums are read and written once per two steps.  Lanes
+// [2, 30) of a warp are written; level 1 also produces the halo row and
+// column the second level needs.  At tick r the input row r enters; level 1
+// computes row r - 1, level 2 row r - 2.
+struct AdjArgs2 {
+    const float *u1, *v1, *w1;  // X^{k+1}
+    const float *u0, *v0, *w0;  // X^k
+    const float *lu, *lv, *lw, *clu, *clv, *clw;  // lam^{k+2}
+    float *luo, *lvo, *lwo, *cluo, *clvo, *clwo;  // lam^k
+    const float *a11, *a12, *a22;
+    float *g11, *g12, *g22;
+    double* partials;
+    int nx, ny, pitch;
+};
+
+template <bool KAHAN, bool EDGE, bool YEDGE>
+__device__ __forceinline__ void adj2_warp(const AdjArgs2& a, const Rates32& k, const int H, const int strip,
+                                          const int chunk, const int lane, double* part)
+{
+    const int nx = a.nx, ny = a.ny, pitch = a.pitch;
+    const int gx = strip * 28 - 2 + lane;
+    const bool ind = EDGE ? (gx >= 0 && gx < nx) : true;
+    const bool hasW = EDGE ? gx > 0 : true, hasE = EDGE ? gx + 1 < nx : true;
+    const bool outc = ind && lane >= 2 && lane < 30;
+    const int ys = chunk * H;
+    const int ye = min(ny, ys + H);
+    const int lo0 = max(0, ys - 2);
+    const int nticks = ye + 2 - lo0;  // level 2 reaches row ye - 1 at tick ye + 1
+    auto inrow = [&](int r) { return ind && r >= 0 && r < ny; };
+    // level-1 input row (lam^{k+2}, X^{k+1}, tensor) and own fields
+    auto load1 = [&](int r, AdjRow& x, float& lu, float& clu, float& a11) {
+        const bool in = inrow(r);
+        const size_t o = (size_t)r * pitch + gx;
+        load_row<KAHAN>(a.u1, a.v1, a.w1, a.lv, a.lw, a.clv, a.clw, a.a12, a.a22, in, o, x);
+        lu = in ? __ldg(a.lu + o) : 0.0f;
+        clu = (in && KAHAN) ? __ldg(a.clu + o) : 0.0f;
+        a11 = in ? __ldg(a.a11 + o) : 0.0f;
+    };
+    // level-2 state row (X^k)
+    auto load0 = [&](int r, float& u, float& v, float& w) {
+        if (inrow(r)) {
+            const size_t o = (size_t)r * pitch + gx;
+            u = __ldg(a.u0 + o); v = __ldg(a.v0 + o); w = __ldg(a.w0 + o);
+        } else {
+            u = v = w = 0.0f;
+        }
+    };
+    RateSums sums;
+    // level-1 window (rows r-2, r-1, r) with own fields of row r-1 / r
+    AdjRow S1, P1, N1;
+    float luP = 0.f, cluP = 0.f, a11P = 0.f, luN = 0.f, cluN = 0.f, a11N = 0.f;
+    // level-2 window: lam^{k+1} rows and X^k rows (r-3, r-2, r-1), tensor rows via level 1's window history
+    AdjRow S2, P2, N2;
+    float lu2P = 0.f, clu2P = 0.f, a11_2P = 0.f;  // own fields of level 2's row
+    float d11c = 0.f, d12c = 0.f, d22c = 0.f;      // level-1 gradient increments of level 2's row
+    float x0u[3] = {0.f, 0.f, 0.f}, x0v[3] = {0.f, 0.f, 0.f}, x0w[3] = {0.f, 0.f, 0.f};
+    S1 = P1 = N1 = AdjRow{};
+    S2 = P2 = N2 = AdjRow{};
+    // prefetch the first input rows
+    AdjRow in1;
+    float inlu, inclu, ina11, in0u, in0v, in0w;
+    load1(lo0, in1, inlu, inclu, ina11);
+    load0(lo0 - 1, in0u, in0v, in0w);
+    float lu1prev = 0.f, clu1prev = 0.f, a11prev = 0.f;  // level-1 outputs of the previous tick
+    AdjOut prev1{};
+    bool prev_own = false;
+    for (int tk = 0; tk < nticks; ++tk) {
+        const int r = lo0 + tk;
+        // input row r enters level 1's window; X^k row r - 1 enters level 2's
+        S1 = P1; P1 = N1; N1 = in1;
+        luP = luN; cluP = cluN; a11P = a11N;
+        luN = inlu; cluN = inclu; a11N = ina11;
+        x0u[0] = x0u[1]; x0u[1] = x0u[2]; x0u[2] = in0u;
+        x0v[0] = x0v[1]; x0v[1] = x0v[2]; x0v[2] = in0v;
+        x0w[0] = x0w[1]; x0w[1] = x0w[2]; x0w[2] = in0w;
+        load1(r + 1, in1, inlu, inclu, ina11);
+        load0(r, in0u, in0v, in0w);
+        // level 1: row q1 = r - 1
+        const int q1 = r - 1;
+        const AdjOut o1 = adj_level<KAHAN, EDGE, YEDGE>(k, S1, P1, N1, luP, cluP, a11P, hasW, hasE, q1 > 0,
+                                                        q1 + 1 < ny);
+        const bool own1 = q1 >= ys && q1 < ye;
+        // level-1 lam^{k+1} row q1 enters level 2's window (with X^k row q1 and the tensor of row q1)
+        AdjRow nw;
+        nw.u = x0u[2]; nw.v = x0v[2]; nw.w = x0w[2];
+        nw.lv = o1.lv; nw.clv = o1.clv; nw.lw = o1.lw; nw.clw = o1.clw;
+        nw.a12 = P1.a12; nw.a22 = P1.a22;
+        S2 = P2; P2 = N2; N2 = nw;
+        // level 2: row q2 = r - 2, own fields from level 1's previous output
+        const int q2 = r - 2;
+        const AdjOut o2 = adj_level<KAHAN, EDGE, YEDGE>(k, S2, P2, N2, lu1prev, clu1prev, a11prev, hasW, hasE,
+                                                        q2 > 0, q2 + 1 < ny);
+        if (q2 >= ys && q2 < ye && outc) {
+            const size_t off = (size_t)q2 * pitch + gx;
+            sums.add_all(o2);
+            if (prev_own) sums.add_all(prev1);
+            a.luo[off] = o2.lu; a.lvo[off] = o2.lv; a.lwo[off] = o2.lw;
+            if (KAHAN) { a.cluo[off] = o2.clu; a.clvo[off] = o2.clv; a.clwo[off] = o2.clw; }
+            a.g11[off] = __ldg(a.g11 + off) + (d11c + o2.d11);
+            a.g12[off] = __ldg(a.g12 + off) + (d12c + o2.d12);
+            a.g22[off] = __ldg(a.g22 + off) + (d22c + o2.d22);
+        }
+        // level 1's row q1 becomes level 2's row at the next tick
+        lu1prev = o1.lu; clu1prev = o1.clu; a11prev = a11P;
+        d11c = o1.d11; d12c = o1.d12; d22c = o1.d22;
+        prev1 = o1;
+        prev_own = own1;
+    }
+    sums.fold(part, lane, k.dt);
+}
+
+template <bool KAHAN>
+__global__ void __launch_bounds__(128, 4) adjoint2_kernel(const AdjArgs2 a, const Rates32 k, const int H,
+                                                          const int nstrips, const int nwarps)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gw >= nwarps) return;
+    const int strip = gw % nstrips, chunk = gw / nstrips;
+    const int gx0 = strip * 28 - 2;
+    double* part = a.partials + (size_t)gw * 4;
+    const int ys = chunk * H;
+    const bool yin = ys - 3 >= 1 && ys + H + 3 <= a.ny - 1;
+    if (gx0 >= 1 && gx0 + 31 <= a.nx - 2) {
+        if (yin) adj2_warp<KAHAN, false, false>(a, k, H, strip, chunk, lane, part);
+        else adj2_warp<KAHAN, false, true>(a, k, H, strip, chunk, lane, part);
+    } else {
+        adj2_warp<KAHAN, true, true>(a, k, H, strip, chunk, lane, part);
+    }
 }
 
 // g64 += g32; g32 = 0 (pitched, 3 fields)
@@ -307,6 +498,9 @@ struct AdjWork {
     double* g64[3] = {};
     double* partials = nullptr;
     int nblocks = 0;
+    // states of the trailing segments kept from the forward pass (no recompute)
+    void* big = nullptr;
+    size_t big_bytes = 0;
 };
 
 }  // namespace
@@ -316,9 +510,17 @@ void gg_release_extras(gg_sim* s)
     if (s && s->adj) {
         AdjWork* w = (AdjWork*)s->adj;
         if (w->base) cudaFree(w->base);
+        if (w->big) cudaFree(w->big);
         delete w;
         s->adj = nullptr;
     }
+}
+
+extern "C" int gg_adjoint_release(gg_sim* s)
+{
+    if (!s) return GG_ERR_ARG;
+    gg_release_extras(s);
+    return GG_OK;
 }
 
 static int adj_workspace(gg_sim* s, int K, int nseg, bool kahan, AdjWork** out)
@@ -326,7 +528,8 @@ static int adj_workspace(gg_sim* s, int K, int nseg, bool kahan, AdjWork** out)
     const size_t fb = ((size_t)s->pitch * s->ny * 4 + 255) / 256 * 256;
     const size_t db = ((size_t)s->pitch * s->ny * 8 + 255) / 256 * 256;
     const int nstate = kahan ? 6 : 3;
-    const int nblocks = adj_warps(s->nx, s->ny);  // one FP64 record of rate gradients per warp
+    // one FP64 record of rate gradients per warp of the larger of the two adjoint launches
+    const int nblocks = std::max(adj_warps(s->nx, s->ny), adj2_warps(s->nx, s->ny));
     const size_t need = fb * ((size_t)nseg * nstate + (size_t)K * 3 + 6 + 12 + 3) + db * 3 +
                         (((size_t)nblocks * 4 * 8 + 255) / 256 * 256);
     AdjWork* w = (AdjWork*)s->adj;
@@ -389,14 +592,110 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
     const int nstate = w->nstate;
     cudaError_t e = cudaSuccess;
 
-    // 1. forward pass, storing the state (with Kahan terms) at the start of every segment
+    const Rates32 r = rates32(s);
+    // recompute depth and chunk height: the simulation's warp plan when it has
+    // one, else single steps
+    const int TR = s->plan.kind == 1 ? s->plan.T : 1;
+    const int HR = s->plan.kind == 1 ? s->plan.by : default_plan(s->nx, s->ny, 1).by;
+    // Runs nsteps steps from the state `in` (u, v, w, cu, cv, cw) in passes of
+    // up to TR steps.  The state after step kk (1 <= kk < nsteps, and nsteps
+    // itself when fin is null) is written to slot(kk) (u, v, w); the last
+    // state goes to fin (u, v, w and Kahan terms) when fin is given.  Kahan
+    // terms between passes alternate between the two scomp buffers.
+    auto passes = [&](float* const in[6], int nsteps, auto slot, float* const* fin) -> cudaError_t {
+        int kk = 0, pass = 0;
+        cudaError_t ee = cudaSuccess;
+        while (kk < nsteps && ee == cudaSuccess) {
+            const int Tp = std::min(TR, nsteps - kk);
+            const bool last = kk + Tp == nsteps && fin;
+            Grid32 g;
+            if (kk == 0) { g.u = in[0]; g.v = in[1]; g.w = in[2]; }
+            else { float* const* x = slot(kk); g.u = x[0]; g.v = x[1]; g.w = x[2]; }
+            g.cu = kahan ? (kk == 0 ? in[3] : w->scomp[pass & 1][0]) : nullptr;
+            g.cv = kahan ? (kk == 0 ? in[4] : w->scomp[pass & 1][1]) : nullptr;
+            g.cw = kahan ? (kk == 0 ? in[5] : w->scomp[pass & 1][2]) : nullptr;
+            if (last) {
+                g.uo = fin[0]; g.vo = fin[1]; g.wo = fin[2];
+                g.cuo = kahan ? fin[3] : nullptr; g.cvo = kahan ? fin[4] : nullptr; g.cwo = kahan ? fin[5] : nullptr;
+            } else {
+                float* const* x = slot(kk + Tp);
+                g.uo = x[0]; g.vo = x[1]; g.wo = x[2];
+                g.cuo = kahan ? w->scomp[(pass + 1) & 1][0] : nullptr;
+                g.cvo = kahan ? w->scomp[(pass + 1) & 1][1] : nullptr;
+                g.cwo = kahan ? w->scomp[(pass + 1) & 1][2] : nullptr;
+            }
+            g.a11 = s->a32[0]; g.a12 = s->a32[1]; g.a22 = s->a32[2];
+            g.nx = s->nx; g.ny = s->ny; g.pitch = s->pitch;
+            Stash32 sh = {};
+            for (int t = 1; t < Tp; ++t) {
+                float* const* x = slot(kk + t);
+                sh.u[t - 1] = x[0]; sh.v[t - 1] = x[1]; sh.w[t - 1] = x[2];
+            }
+            ee = launch_stepw_stash(g, r, HR, Tp, kahan, sh, st);
+            kk += Tp;
+            ++pass;
+        }
+        return ee;
+    };
+
+    // Trailing segments whose states fit in 60 % of the free device memory are
+    // kept from the forward pass and need no recomputation.
+    int ns = 0;
+    {
+        size_t freeb = 0, totalb = 0;
+        if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) { cudaGetLastError(); freeb = 0; }
+        const size_t per_seg = (size_t)K * 3 * ((fbytes + 255) / 256 * 256);
+        const size_t have = w->big_bytes;
+        // 60 % of (what this workspace already holds + what is free): the same
+        // budget on every call, so a second call reuses the first call's buffer
+        const size_t budget = (have + freeb) / 10 * 6;
+        ns = (int)std::min<size_t>((size_t)nseg, per_seg ? budget / per_seg : 0);
+        const size_t need = (size_t)ns * per_seg;
+        if (ns > 0 && need > have) {
+            if (w->big) cudaFree(w->big);
+            w->big = nullptr;
+            w->big_bytes = 0;
+            if (cudaMalloc(&w->big, need) != cudaSuccess) {
+                cudaGetLastError();
+                w->big = nullptr;
+                ns = 0;
+            } else {
+                w->big_bytes = need;
+            }
+        }
+    }
+    const int seg_kept = nseg - ns;  // segments >= seg_kept are stored, not recomputed
+    const size_t fstride = (fbytes + 255) / 256 * 256;
+    auto big_slot = [&](int seg, int kk, float** out3) {
+        char* b = (char*)w->big + ((size_t)(seg - seg_kept) * K + kk) * 3 * fstride;
+        out3[0] = (float*)b; out3[1] = (float*)(b + fstride); out3[2] = (float*)(b + 2 * fstride);
+    };
+
+    // 1. forward pass, storing the state (with Kahan terms) at the start of every
+    // segment and every state of the trailing segments
     for (int seg = 0; seg < nseg && e == cudaSuccess; ++seg) {
         for (int f = 0; f < nstate && e == cudaSuccess; ++f)
             e = cudaMemcpyAsync(w->ckpt[(size_t)seg * nstate + f], s->f32[s->cur][f], fbytes, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) break;
         const int64_t len = std::min<int64_t>(K, N - (int64_t)seg * K);
-        rc = gg_step(s, len);
-        if (rc != GG_OK) return rc;
+        if (seg < seg_kept) {
+            rc = gg_step(s, len);
+            if (rc != GG_OK) return rc;
+        } else {
+            float* in[6] = {s->f32[s->cur][0], s->f32[s->cur][1], s->f32[s->cur][2],
+                            kahan ? s->f32[s->cur][3] : nullptr, kahan ? s->f32[s->cur][4] : nullptr,
+                            kahan ? s->f32[s->cur][5] : nullptr};
+            const int o = s->cur ^ 1;
+            float* fin[6] = {s->f32[o][0], s->f32[o][1], s->f32[o][2], kahan ? s->f32[o][3] : nullptr,
+                             kahan ? s->f32[o][4] : nullptr, kahan ? s->f32[o][5] : nullptr};
+            float* tmp[3];
+            auto slot = [&](int kk) -> float* const* {
+                big_slot(seg, kk, tmp);
+                return tmp;
+            };
+            e = passes(in, (int)len, slot, fin);
+            if (e == cudaSuccess) { s->cur ^= 1; s->steps += len; }
+        }
     }
     // 2. lam^N = dL/dX^N (zero when not given); Kahan terms and gradient sums start at 0
     const float* dl[3] = {dLdu_N, dLdv_N, dLdw_N};
@@ -408,13 +707,10 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
     if (e == cudaSuccess) e = cudaMemsetAsync(w->partials, 0, (size_t)w->nblocks * 4 * 8, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "adjoint setup");
 
-    const Rates32 r = rates32(s);
-    // recompute depth and chunk height: the simulation's warp plan when it has
-    // one, else single steps
-    const int TR = s->plan.kind == 1 ? s->plan.T : 1;
-    const int HR = s->plan.kind == 1 ? s->plan.by : default_plan(s->nx, s->ny, 1).by;
     const int aH = adj_chunk(s->nx, s->ny), astrips = adj_strips(s->nx), awarps = adj_warps(s->nx, s->ny);
     const int ablocks = (awarps + 3) / 4;
+    const int a2H = adj2_chunk(s->nx, s->ny), a2strips = adj2_strips(s->nx), a2warps = adj2_warps(s->nx, s->ny);
+    const int a2blocks = (a2warps + 3) / 4;
     int lb = 0;          // current lam buffer
     int since_flush = 0;
     auto flush = [&]() {
@@ -426,44 +722,37 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
     // 3. segments in reverse: recompute the states of the segment, then run its adjoint steps
     for (int seg = nseg - 1; seg >= 0 && e == cudaSuccess; --seg) {
         const int len = (int)std::min<int64_t>(K, N - (int64_t)seg * K);
+        const bool kept = seg >= seg_kept;
         auto state = [&](int kk, int f) -> float* {  // u, v, w of X^{seg*K + kk}
-            return kk == 0 ? w->ckpt[(size_t)seg * nstate + f] : w->stash[(size_t)kk * 3 + f];
-        };
-        auto comp = [&](int kk, int f) -> float* {  // Kahan terms of the segment's first state
-            (void)kk;
-            return kahan ? w->ckpt[(size_t)seg * nstate + 3 + f] : nullptr;
-        };
-        // Recompute X^{seg K + 1 .. seg K + len - 1} in passes of up to TR steps;
-        // the intermediate levels of a pass write their states straight into
-        // the stash, the Kahan terms alternate between two buffers per pass.
-        int kk = 0, pass = 0;
-        while (kk + 1 < len && e == cudaSuccess) {
-            const int Tp = std::min(TR, len - 1 - kk);
-            Grid32 g;
-            g.u = state(kk, 0); g.v = state(kk, 1); g.w = state(kk, 2);
-            const bool first = kk == 0;
-            g.cu = kahan ? (first ? comp(0, 0) : w->scomp[pass & 1][0]) : nullptr;
-            g.cv = kahan ? (first ? comp(0, 1) : w->scomp[pass & 1][1]) : nullptr;
-            g.cw = kahan ? (first ? comp(0, 2) : w->scomp[pass & 1][2]) : nullptr;
-            g.uo = state(kk + Tp, 0); g.vo = state(kk + Tp, 1); g.wo = state(kk + Tp, 2);
-            g.cuo = kahan ? w->scomp[(pass + 1) & 1][0] : nullptr;
-            g.cvo = kahan ? w->scomp[(pass + 1) & 1][1] : nullptr;
-            g.cwo = kahan ? w->scomp[(pass + 1) & 1][2] : nullptr;
-            g.a11 = s->a32[0]; g.a12 = s->a32[1]; g.a22 = s->a32[2];
-            g.nx = s->nx; g.ny = s->ny; g.pitch = s->pitch;
-            Stash32 sh = {};
-            for (int t = 1; t < Tp; ++t) {
-                sh.u[t - 1] = state(kk + t, 0);
-                sh.v[t - 1] = state(kk + t, 1);
-                sh.w[t - 1] = state(kk + t, 2);
+            if (kk == 0) return w->ckpt[(size_t)seg * nstate + f];
+            if (kept) {
+                float* x[3];
+                big_slot(seg, kk, x);
+                return x[f];
             }
-            e = launch_stepw_stash(g, r, HR, Tp, kahan, sh, st);
-            kk += Tp;
-            ++pass;
+            return w->stash[(size_t)kk * 3 + f];
+        };
+        if (!kept && len > 1) {
+            // recompute X^{seg K + 1 .. seg K + len - 1} into the stash
+            float* in[6] = {state(0, 0), state(0, 1), state(0, 2),
+                            kahan ? w->ckpt[(size_t)seg * nstate + 3] : nullptr,
+                            kahan ? w->ckpt[(size_t)seg * nstate + 4] : nullptr,
+                            kahan ? w->ckpt[(size_t)seg * nstate + 5] : nullptr};
+            float* tmp[3];
+            auto slot = [&](int kk) -> float* const* {
+                tmp[0] = w->stash[(size_t)kk * 3 + 0];
+                tmp[1] = w->stash[(size_t)kk * 3 + 1];
+                tmp[2] = w->stash[(size_t)kk * 3 + 2];
+                return tmp;
+            };
+            e = passes(in, len - 1, slot, nullptr);
         }
-        for (int kk = len - 1; kk >= 0 && e == cudaSuccess; --kk) {
+        // reverse sweep of the segment: an odd first step alone, then pairs of
+        // steps (kk, kk - 1) in one two-level pass
+        int kr = len - 1;
+        auto single = [&](int k1) {
             AdjArgs a;
-            a.u = state(kk, 0); a.v = state(kk, 1); a.w = state(kk, 2);
+            a.u = state(k1, 0); a.v = state(k1, 1); a.w = state(k1, 2);
             a.lu = w->lam[lb][0]; a.lv = w->lam[lb][1]; a.lw = w->lam[lb][2];
             a.clu = w->lam[lb][3]; a.clv = w->lam[lb][4]; a.clw = w->lam[lb][5];
             a.luo = w->lam[lb ^ 1][0]; a.lvo = w->lam[lb ^ 1][1]; a.lwo = w->lam[lb ^ 1][2];
@@ -474,9 +763,35 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
             a.nx = s->nx; a.ny = s->ny; a.pitch = s->pitch;
             if (kahan) adjoint_step_kernel<true><<<ablocks, 128, 0, st>>>(a, r, aH, astrips, awarps);
             else adjoint_step_kernel<false><<<ablocks, 128, 0, st>>>(a, r, aH, astrips, awarps);
-            e = cudaGetLastError();
             lb ^= 1;
-            if (e == cudaSuccess && ++since_flush == kFlushEvery) e = flush();
+            since_flush += 1;
+            return cudaGetLastError();
+        };
+        auto pair = [&](int k1) {  // steps k1 and k1 - 1
+            AdjArgs2 a;
+            a.u1 = state(k1, 0); a.v1 = state(k1, 1); a.w1 = state(k1, 2);
+            a.u0 = state(k1 - 1, 0); a.v0 = state(k1 - 1, 1); a.w0 = state(k1 - 1, 2);
+            a.lu = w->lam[lb][0]; a.lv = w->lam[lb][1]; a.lw = w->lam[lb][2];
+            a.clu = w->lam[lb][3]; a.clv = w->lam[lb][4]; a.clw = w->lam[lb][5];
+            a.luo = w->lam[lb ^ 1][0]; a.lvo = w->lam[lb ^ 1][1]; a.lwo = w->lam[lb ^ 1][2];
+            a.cluo = w->lam[lb ^ 1][3]; a.clvo = w->lam[lb ^ 1][4]; a.clwo = w->lam[lb ^ 1][5];
+            a.a11 = s->a32[0]; a.a12 = s->a32[1]; a.a22 = s->a32[2];
+            a.g11 = w->g32[0]; a.g12 = w->g32[1]; a.g22 = w->g32[2];
+            a.partials = w->partials;
+            a.nx = s->nx; a.ny = s->ny; a.pitch = s->pitch;
+            if (kahan) adjoint2_kernel<true><<<a2blocks, 128, 0, st>>>(a, r, a2H, a2strips, a2warps);
+            else adjoint2_kernel<false><<<a2blocks, 128, 0, st>>>(a, r, a2H, a2strips, a2warps);
+            lb ^= 1;
+            since_flush += 2;
+            return cudaGetLastError();
+        };
+        if ((len & 1) && e == cudaSuccess) {
+            e = single(kr);
+            --kr;
+        }
+        for (; kr >= 1 && e == cudaSuccess; kr -= 2) {
+            e = pair(kr);
+            if (e == cudaSuccess && since_flush >= kFlushEvery) e = flush();
         }
     }
     if (e == cudaSuccess && since_flush) e = flush();

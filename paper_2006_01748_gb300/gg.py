@@ -79,6 +79,7 @@ _SIGNATURES = {
     "gg_diagnostics_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _I32, _I32, _I32, _I32, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double, _VP, ctypes.POINTER(gg_diag)]),
     "gg_adjoint": (ctypes.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _DP, _I64]),
+    "gg_adjoint_release": (ctypes.c_int, [_VP]),
     "gg_autotune": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(_I32)]),
     "gg_set_plan": (ctypes.c_int, [_VP, _I32, _I32, _I32, _I32]),
     "gg_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
@@ -159,6 +160,10 @@ def gg_diagnostics(sim, eps=None):
 def gg_adjoint(sim, nsteps, dLdu, dLdv, dLdw, g_theta, g_l1, g_l2, g_u0, g_v0, g_w0, g_scalars, checkpoint_every=0):
     return lib().gg_adjoint(sim, int(nsteps), dLdu, dLdv, dLdw, g_theta, g_l1, g_l2, g_u0, g_v0, g_w0,
                             g_scalars, int(checkpoint_every))
+
+
+def gg_adjoint_release(sim):
+    return lib().gg_adjoint_release(sim)
 
 
 def gg_dt(sim):
@@ -360,6 +365,10 @@ class GGSim:
         _check(rc, self._sim, "gg_adjoint")
         res["scalars"] = gs
         return res
+
+    def release_adjoint(self):
+        """Free the adjoint workspace (checkpoints, stash and kept states)."""
+        _check(gg_adjoint_release(self._sim), self._sim, "gg_adjoint_release")
 
     def state(self, fp64: bool = True):
         return tuple(self.read(f, fp64) for f in ("u", "v", "w"))

@@ -6,8 +6,8 @@
     python -m paper_2006_01748_gb300.prof plans --nx 4096
         3 passes of each warp plan (T = 1..4, chunks 64/128/256, Kahan) and of
         the plain FP32 T = 1 plan, one line per plan on stdout
-    python -m paper_2006_01748_gb300.prof adjoint --nx 2048 --steps 20
-        one gg_adjoint call on the adjoint workload
+    python -m paper_2006_01748_gb300.prof adjoint --nx 2048 --steps 20 --T 3 --chunk 128
+        one gg_adjoint call on the adjoint workload (forward plan fixed, no tuning)
     python -m paper_2006_01748_gb300.prof batch --scale 1 --steps 6
         the 256-instance ensemble, tuned, a few steps
 
@@ -54,7 +54,9 @@ def _adjoint(args):
     from . import build, gg, inputs
     build()
     p = inputs.adjoint_2048(nx=args.nx, steps=args.steps)
-    with gg.GGSim.from_problem(p, precision="fp32_kahan") as sim:
+    # a fixed plan (the autotuner's choice at 2048^2), so that no tuning launches run
+    with gg.GGSim.from_problem(p, precision="fp32_kahan", steps_per_pass=1) as sim:
+        sim.set_plan("warp", args.T, chunk=args.chunk)
         t = torch.full((p.cells,), 1.0 / p.cells, dtype=torch.float32, device="cuda")
         r = sim.adjoint(args.steps, None, t, t, outputs=("theta",))
         torch.cuda.synchronize()
@@ -91,6 +93,8 @@ def main(argv=None):
     s = sub.add_parser("adjoint")
     s.add_argument("--nx", type=int, default=2048)
     s.add_argument("--steps", type=int, default=20)
+    s.add_argument("--T", type=int, default=3)
+    s.add_argument("--chunk", type=int, default=128)
     s.set_defaults(fn=_adjoint)
     s = sub.add_parser("batch")
     s.add_argument("--scale", type=int, default=1)

@@ -89,17 +89,49 @@ def test_adjoint_without_kahan_and_without_reactions(torch):
 
 
 def test_checkpoint_spacing_does_not_change_the_result(torch):
+    """The recomputed states are bitwise those of the forward pass for every
+    checkpoint spacing K; only the grouping of the reverse sweep into single
+    and paired adjoint steps (and so the rounding of the per-cell gradient
+    sums) depends on K."""
     nx, ny, steps = 70, 50, 97
     p = small_problem(nx, ny, steps=steps)
     dU = inputs.white_noise(nx, ny, 1, -1, 1)
     dV = inputs.white_noise(nx, ny, 2, -1, 1)
     dW = inputs.white_noise(nx, ny, 3, -1, 1)
     base = gpu_adjoint(torch, p, steps, dU, dV, dW, checkpoint_every=0)
-    for K in (1, 7, 97, 500):
+    for K in (1, 7, 96, 97, 500):
         r = gpu_adjoint(torch, p, steps, dU, dV, dW, checkpoint_every=K)
         for k in ("theta", "lambda1", "lambda2", "u0", "v0", "w0"):
-            assert np.array_equal(r[k], base[k]), (K, k)
-        assert np.array_equal(r["scalars"], base["scalars"])
+            assert rel_err(r[k], base[k]) <= 1e-6, (K, k)
+        assert np.allclose(r["scalars"], base["scalars"], rtol=1e-6, atol=0)
+
+
+def test_workspace_reuse_and_release(torch):
+    """A second call on the same simulation reuses the workspace (kept
+    states included) and a call after gg_adjoint_release allocates it again;
+    from the same state both give the first call's bits."""
+    nx, ny, steps = 70, 50, 97
+    p = small_problem(nx, ny, steps=steps)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda().view(-1)
+    dV = t(inputs.white_noise(nx, ny, 2, -1, 1))
+    with gg.GGSim.from_problem(p, precision="fp32_kahan") as sim:
+        names = ("u", "v", "w", "comp_u", "comp_v", "comp_w")
+        x0 = [sim.read(f, fp64=False) for f in names]
+
+        def run():
+            for f, x in zip(names, x0):
+                sim.write(f, x)
+            r = sim.adjoint(steps, None, dV, None)
+            return {k: (v.cpu().numpy() if k != "scalars" else v) for k, v in r.items()}
+
+        first = run()
+        again = run()
+        sim.release_adjoint()
+        sim.release_adjoint()  # a no-op without a workspace
+        after = run()
+        for r in (again, after):
+            for k in first:
+                assert np.array_equal(r[k], first[k]), k
 
 
 def _fp64_loss(p, dt, steps, Vstar, **over):
