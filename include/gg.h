@@ -69,9 +69,20 @@ extern "C" {
 #define GG_FIELD_COMP_U  3  /* Kahan compensation terms (GG_FP32_KAHAN only) */
 #define GG_FIELD_COMP_V  4
 #define GG_FIELD_COMP_W  5
-#define GG_FIELD_A11     6  /* read only: tensor entries as used by the kernels */
+/* read only: the entries a11, a12, a22 of eq. (2) per cell (for FP32
+ * simulations computed in FP64 on read from theta, lambda1, lambda2 and
+ * rounded to the destination type) */
+#define GG_FIELD_A11     6
 #define GG_FIELD_A12     7
 #define GG_FIELD_A22     8
+/* read only, FP32 simulations only: the coefficients the FP32 kernels read,
+ * built once in FP64 and rounded to float (Table 2's weights):
+ *   FACE_X(i,j) = (a11(i,j) + a11(i+1,j)) / (2 dx^2), 0 on the last column;
+ *   FACE_Y(i,j) = (a22(i,j) + a22(i,j+1)) / (2 dy^2), 0 on the last row;
+ *   CROSS(i,j)  = a12(i,j) / (4 dx dy). */
+#define GG_FIELD_FACE_X  9
+#define GG_FIELD_FACE_Y  10
+#define GG_FIELD_CROSS   11
 
 /* ---- gg_params.flags ---- */
 #define GG_FLAG_NO_REACTION     1  /* drop U(1-U) - delta U W, rho V(1-V), c(V-W) */

@@ -63,7 +63,7 @@ struct AdjArgs {
     const float *u, *v, *w;                          // X^k
     const float *lu, *lv, *lw, *clu, *clv, *clw;     // lam^{k+1} and its Kahan terms
     float *luo, *lvo, *lwo, *cluo, *clvo, *clwo;     // lam^k
-    const float *a11, *a12, *a22;
+    const float *ax, *b, *ay;                        // face / cross weights (Grid32)
     float *g11, *g12, *g22;                          // FP32 per-cell sums (in place)
     double* partials;                                // [blocks][4]: delta, rho, D, c
     int nx, ny, pitch;
@@ -84,10 +84,10 @@ __device__ __forceinline__ float from_east(float x) { return __shfl_down_sync(kF
 // One row of the inputs of an adjoint step at one column: the fields read on
 // rows q-1, q, q+1 (AdjRow) and those read on row q only (AdjOwn).
 struct AdjRow {
-    float u, v, w, lv, lw, clv, clw, a12, a22;
+    float u, v, w, lv, lw, clv, clw, b, ay;
 };
 struct AdjOwn {
-    float lu, clu, a11, g11, g12, g22;
+    float lu, clu, ax, g11, g12, g22;
 };
 // Result of one adjoint level at one cell: lam at step k with its Kahan
 // terms, dt times the tensor-gradient increments, the four rate terms.
@@ -98,11 +98,11 @@ struct AdjOut {
 };
 
 // One adjoint step at row q of one lane, from the rows S (q-1), P (q), N (q+1)
-// of lam^{k+1} and X^k and the own-row fields lu, clu, a11.  All lanes of the
-// warp call it (it shuffles).
+// of lam^{k+1} and X^k and the own-row fields lu, clu and ax (east-face
+// weight).  All lanes of the warp call it (it shuffles).
 template <bool KAHAN, bool EDGE, bool YEDGE = true>
 __device__ __forceinline__ AdjOut adj_level(const Rates32& k, const AdjRow& S, const AdjRow& P, const AdjRow& N,
-                                            float lu, float clu, float a11, bool hasW, bool hasE, bool hasS_,
+                                            float lu, float clu, float ax, bool hasW, bool hasE, bool hasS_,
                                             bool hasN_)
 {
     // interior chunks (YEDGE false) have both the south and the north face
@@ -120,19 +120,19 @@ __device__ __forceinline__ AdjOut adj_level(const Rates32& k, const AdjRow& S, c
     if (EDGE && !hasW) { LxW_P = LxW_N = LxW_S = 0.0f; }
     const float LyN = hasN ? dW(P.lw, P.clw, N.lw, N.clw) : 0.0f;
     const float LyS = hasS ? dW(S.lw, S.clw, P.lw, P.clw) : 0.0f;
-    // transpose of the a12 cross terms (mirrored central differences)
-    const float SxP = P.a12 * (LxE_P + LxW_P), SxN = N.a12 * (LxE_N + LxW_N), SxS = S.a12 * (LxE_S + LxW_S);
-    const float SyP = P.a12 * (LyN + LyS);
+    // transpose of the a12 cross terms (mirrored central differences; b
+    // carries the factor 1/(4 dx dy))
+    const float SxP = P.b * (LxE_P + LxW_P), SxN = N.b * (LxE_N + LxW_N), SxS = S.b * (LxE_S + LxW_S);
+    const float SyP = P.b * (LyN + LyS);
     float SyE = from_east(SyP), SyW = from_west(SyP);
     const float Ty = (hasS ? SxS : 0.0f) - (hasN ? SxN : 0.0f) + SxP * ((hasN ? 0.0f : 1.0f) - (hasS ? 0.0f : 1.0f));
     float Tx;
     if (EDGE) Tx = (hasW ? SyW : 0.0f) - (hasE ? SyE : 0.0f) + SyP * ((hasE ? 0.0f : 1.0f) - (hasW ? 0.0f : 1.0f));
     else Tx = SyW - SyE;
-    float a11E = from_east(a11), a11W = from_west(a11);
-    if (EDGE) { if (!hasE) a11E = a11; if (!hasW) a11W = a11; }
-    const float a22N = hasN ? N.a22 : P.a22, a22S = hasS ? S.a22 : P.a22;
-    const float D2T = ((a11 + a11E) * (-LxE_P) + (a11W + a11) * LxW_P) * k.kx +
-                      ((P.a22 + a22N) * (-LyN) + (a22S + P.a22) * LyS) * k.ky + (Tx + Ty) * k.kc;
+    // face weights: east ax, west = the west lane's ax, north P.ay, south
+    // S.ay (a boundary face has L = 0, so its weight does not matter)
+    const float axW = from_west(ax);
+    const float D2T = (ax * (-LxE_P) + axW * LxW_P) + (P.ay * (-LyN) + S.ay * LyS) + (Tx + Ty);
 
     // state and lamV neighbourhood (mirrored at the boundary)
     float uE = from_east(P.u), uW = from_west(P.u), vE = from_east(P.v), vW = from_west(P.v);
@@ -221,17 +221,17 @@ struct RateSums {
 // Loads of one row at one column (zeros outside the domain).
 template <bool KAHAN>
 __device__ __forceinline__ void load_row(const float* u, const float* v, const float* w, const float* lv,
-                                         const float* lw, const float* clv, const float* clw, const float* a12,
-                                         const float* a22, bool in, size_t o, AdjRow& x)
+                                         const float* lw, const float* clv, const float* clw, const float* b,
+                                         const float* ay, bool in, size_t o, AdjRow& x)
 {
     if (in) {
         x.u = __ldg(u + o); x.v = __ldg(v + o); x.w = __ldg(w + o);
         x.lv = __ldg(lv + o); x.lw = __ldg(lw + o);
         if (KAHAN) { x.clv = __ldg(clv + o); x.clw = __ldg(clw + o); }
         else { x.clv = x.clw = 0.0f; }
-        x.a12 = __ldg(a12 + o); x.a22 = __ldg(a22 + o);
+        x.b = __ldg(b + o); x.ay = __ldg(ay + o);
     } else {
-        x.u = x.v = x.w = x.lv = x.lw = x.clv = x.clw = x.a12 = x.a22 = 0.0f;
+        x.u = x.v = x.w = x.lv = x.lw = x.clv = x.clw = x.b = x.ay = 0.0f;
     }
 }
 
@@ -251,7 +251,7 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
     const int ys = chunk * H;
     const int ye = min(ny, ys + H);
     auto load = [&](int r, AdjRow& x) {
-        load_row<KAHAN>(a.u, a.v, a.w, a.lv, a.lw, a.clv, a.clw, a.a12, a.a22, ind && r >= 0 && r < ny,
+        load_row<KAHAN>(a.u, a.v, a.w, a.lv, a.lw, a.clv, a.clw, a.b, a.ay, ind && r >= 0 && r < ny,
                         (size_t)r * pitch + gx, x);
     };
     auto load_own = [&](int r, AdjOwn& x) {
@@ -259,10 +259,10 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
             const size_t o = (size_t)r * pitch + gx;
             x.lu = __ldg(a.lu + o);
             x.clu = KAHAN ? __ldg(a.clu + o) : 0.0f;
-            x.a11 = __ldg(a.a11 + o);
+            x.ax = __ldg(a.ax + o);
             x.g11 = __ldg(a.g11 + o); x.g12 = __ldg(a.g12 + o); x.g22 = __ldg(a.g22 + o);
         } else {
-            x.lu = x.clu = x.a11 = x.g11 = x.g12 = x.g22 = 0.0f;
+            x.lu = x.clu = x.ax = x.g11 = x.g12 = x.g22 = 0.0f;
         }
     };
     RateSums sums;
@@ -277,7 +277,7 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
         AdjRow nn;
         load(q + 3, nn);
         load_own(q + 1, NO);
-        const AdjOut o = adj_level<KAHAN, EDGE, YEDGE>(k, S, P, N, PO.lu, PO.clu, PO.a11, hasW, hasE, q > 0,
+        const AdjOut o = adj_level<KAHAN, EDGE, YEDGE>(k, S, P, N, PO.lu, PO.clu, PO.ax, hasW, hasE, q > 0,
                                                        q + 1 < ny);
         if (outc) {
             const size_t off = (size_t)q * pitch + gx;
@@ -329,7 +329,7 @@ struct AdjArgs2 {
     const float *u0, *v0, *w0;  // X^k
     const float *lu, *lv, *lw, *clu, *clv, *clw;  // lam^{k+2}
     float *luo, *lvo, *lwo, *cluo, *clvo, *clwo;  // lam^k
-    const float *a11, *a12, *a22;
+    const float *ax, *b, *ay;
     float *g11, *g12, *g22;
     double* partials;
     int nx, ny, pitch;
@@ -350,13 +350,13 @@ __device__ __forceinline__ void adj2_warp(const AdjArgs2& a, const Rates32& k, c
     const int nticks = ye + 2 - lo0;  // level 2 reaches row ye - 1 at tick ye + 1
     auto inrow = [&](int r) { return ind && r >= 0 && r < ny; };
     // level-1 input row (lam^{k+2}, X^{k+1}, tensor) and own fields
-    auto load1 = [&](int r, AdjRow& x, float& lu, float& clu, float& a11) {
+    auto load1 = [&](int r, AdjRow& x, float& lu, float& clu, float& ax) {
         const bool in = inrow(r);
         const size_t o = (size_t)r * pitch + gx;
-        load_row<KAHAN>(a.u1, a.v1, a.w1, a.lv, a.lw, a.clv, a.clw, a.a12, a.a22, in, o, x);
+        load_row<KAHAN>(a.u1, a.v1, a.w1, a.lv, a.lw, a.clv, a.clw, a.b, a.ay, in, o, x);
         lu = in ? __ldg(a.lu + o) : 0.0f;
         clu = (in && KAHAN) ? __ldg(a.clu + o) : 0.0f;
-        a11 = in ? __ldg(a.a11 + o) : 0.0f;
+        ax = in ? __ldg(a.ax + o) : 0.0f;
     };
     // level-2 state row (X^k)
     auto load0 = [&](int r, float& u, float& v, float& w) {
@@ -370,47 +370,46 @@ __device__ __forceinline__ void adj2_warp(const AdjArgs2& a, const Rates32& k, c
     RateSums sums;
     // level-1 window (rows r-2, r-1, r) with own fields of row r-1 / r
     AdjRow S1, P1, N1;
-    float luP = 0.f, cluP = 0.f, a11P = 0.f, luN = 0.f, cluN = 0.f, a11N = 0.f;
+    float luP = 0.f, cluP = 0.f, axP = 0.f, luN = 0.f, cluN = 0.f, axN = 0.f;
     // level-2 window: lam^{k+1} rows and X^k rows (r-3, r-2, r-1), tensor rows via level 1's window history
     AdjRow S2, P2, N2;
-    float lu2P = 0.f, clu2P = 0.f, a11_2P = 0.f;  // own fields of level 2's row
     float d11c = 0.f, d12c = 0.f, d22c = 0.f;      // level-1 gradient increments of level 2's row
     float x0u[3] = {0.f, 0.f, 0.f}, x0v[3] = {0.f, 0.f, 0.f}, x0w[3] = {0.f, 0.f, 0.f};
     S1 = P1 = N1 = AdjRow{};
     S2 = P2 = N2 = AdjRow{};
     // prefetch the first input rows
     AdjRow in1;
-    float inlu, inclu, ina11, in0u, in0v, in0w;
-    load1(lo0, in1, inlu, inclu, ina11);
+    float inlu, inclu, inax, in0u, in0v, in0w;
+    load1(lo0, in1, inlu, inclu, inax);
     load0(lo0 - 1, in0u, in0v, in0w);
-    float lu1prev = 0.f, clu1prev = 0.f, a11prev = 0.f;  // level-1 outputs of the previous tick
+    float lu1prev = 0.f, clu1prev = 0.f, axprev = 0.f;  // level-1 outputs of the previous tick
     AdjOut prev1{};
     bool prev_own = false;
     for (int tk = 0; tk < nticks; ++tk) {
         const int r = lo0 + tk;
         // input row r enters level 1's window; X^k row r - 1 enters level 2's
         S1 = P1; P1 = N1; N1 = in1;
-        luP = luN; cluP = cluN; a11P = a11N;
-        luN = inlu; cluN = inclu; a11N = ina11;
+        luP = luN; cluP = cluN; axP = axN;
+        luN = inlu; cluN = inclu; axN = inax;
         x0u[0] = x0u[1]; x0u[1] = x0u[2]; x0u[2] = in0u;
         x0v[0] = x0v[1]; x0v[1] = x0v[2]; x0v[2] = in0v;
         x0w[0] = x0w[1]; x0w[1] = x0w[2]; x0w[2] = in0w;
-        load1(r + 1, in1, inlu, inclu, ina11);
+        load1(r + 1, in1, inlu, inclu, inax);
         load0(r, in0u, in0v, in0w);
         // level 1: row q1 = r - 1
         const int q1 = r - 1;
-        const AdjOut o1 = adj_level<KAHAN, EDGE, YEDGE>(k, S1, P1, N1, luP, cluP, a11P, hasW, hasE, q1 > 0,
+        const AdjOut o1 = adj_level<KAHAN, EDGE, YEDGE>(k, S1, P1, N1, luP, cluP, axP, hasW, hasE, q1 > 0,
                                                         q1 + 1 < ny);
         const bool own1 = q1 >= ys && q1 < ye;
         // level-1 lam^{k+1} row q1 enters level 2's window (with X^k row q1 and the tensor of row q1)
         AdjRow nw;
         nw.u = x0u[2]; nw.v = x0v[2]; nw.w = x0w[2];
         nw.lv = o1.lv; nw.clv = o1.clv; nw.lw = o1.lw; nw.clw = o1.clw;
-        nw.a12 = P1.a12; nw.a22 = P1.a22;
+        nw.b = P1.b; nw.ay = P1.ay;
         S2 = P2; P2 = N2; N2 = nw;
         // level 2: row q2 = r - 2, own fields from level 1's previous output
         const int q2 = r - 2;
-        const AdjOut o2 = adj_level<KAHAN, EDGE, YEDGE>(k, S2, P2, N2, lu1prev, clu1prev, a11prev, hasW, hasE,
+        const AdjOut o2 = adj_level<KAHAN, EDGE, YEDGE>(k, S2, P2, N2, lu1prev, clu1prev, axprev, hasW, hasE,
                                                         q2 > 0, q2 + 1 < ny);
         if (q2 >= ys && q2 < ye && outc) {
             const size_t off = (size_t)q2 * pitch + gx;
@@ -423,7 +422,7 @@ __device__ __forceinline__ void adj2_warp(const AdjArgs2& a, const Rates32& k, c
             a.g22[off] = __ldg(a.g22 + off) + (d22c + o2.d22);
         }
         // level 1's row q1 becomes level 2's row at the next tick
-        lu1prev = o1.lu; clu1prev = o1.clu; a11prev = a11P;
+        lu1prev = o1.lu; clu1prev = o1.clu; axprev = axP;
         d11c = o1.d11; d12c = o1.d12; d22c = o1.d22;
         prev1 = o1;
         prev_own = own1;
@@ -624,7 +623,7 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
                 g.cvo = kahan ? w->scomp[(pass + 1) & 1][1] : nullptr;
                 g.cwo = kahan ? w->scomp[(pass + 1) & 1][2] : nullptr;
             }
-            g.a11 = s->a32[0]; g.a12 = s->a32[1]; g.a22 = s->a32[2];
+            g.ax = s->a32[0]; g.b = s->a32[1]; g.ay = s->a32[2];
             g.nx = s->nx; g.ny = s->ny; g.pitch = s->pitch;
             Stash32 sh = {};
             for (int t = 1; t < Tp; ++t) {
@@ -757,7 +756,7 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
             a.clu = w->lam[lb][3]; a.clv = w->lam[lb][4]; a.clw = w->lam[lb][5];
             a.luo = w->lam[lb ^ 1][0]; a.lvo = w->lam[lb ^ 1][1]; a.lwo = w->lam[lb ^ 1][2];
             a.cluo = w->lam[lb ^ 1][3]; a.clvo = w->lam[lb ^ 1][4]; a.clwo = w->lam[lb ^ 1][5];
-            a.a11 = s->a32[0]; a.a12 = s->a32[1]; a.a22 = s->a32[2];
+            a.ax = s->a32[0]; a.b = s->a32[1]; a.ay = s->a32[2];
             a.g11 = w->g32[0]; a.g12 = w->g32[1]; a.g22 = w->g32[2];
             a.partials = w->partials;
             a.nx = s->nx; a.ny = s->ny; a.pitch = s->pitch;
@@ -775,7 +774,7 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
             a.clu = w->lam[lb][3]; a.clv = w->lam[lb][4]; a.clw = w->lam[lb][5];
             a.luo = w->lam[lb ^ 1][0]; a.lvo = w->lam[lb ^ 1][1]; a.lwo = w->lam[lb ^ 1][2];
             a.cluo = w->lam[lb ^ 1][3]; a.clvo = w->lam[lb ^ 1][4]; a.clwo = w->lam[lb ^ 1][5];
-            a.a11 = s->a32[0]; a.a12 = s->a32[1]; a.a22 = s->a32[2];
+            a.ax = s->a32[0]; a.b = s->a32[1]; a.ay = s->a32[2];
             a.g11 = w->g32[0]; a.g12 = w->g32[1]; a.g22 = w->g32[2];
             a.partials = w->partials;
             a.nx = s->nx; a.ny = s->ny; a.pitch = s->pitch;

@@ -38,22 +38,28 @@ double stable_dt_max(double dx, double dy, double Lambda, const gg_params& p)
     return 1.0 / (2.0 * L * (1.0 / (dx * dx) + 1.0 / (dy * dy)) + (p.c + p.rho + 1.0 + p.delta));
 }
 
-Rates32 rates32(const gg_sim* s)
+Rates32 make_rates32(double dx, double dy, double dt, const gg_params& p)
 {
     Rates32 r;
-    r.dt = (float)s->dt;
-    r.D = (float)s->params.D;
-    r.delta = (float)s->params.delta;
-    r.rho = (float)s->params.rho;
-    r.c = (float)s->params.c;
-    r.kx = (float)(0.5 / (s->dx * s->dx));
-    r.ky = (float)(0.5 / (s->dy * s->dy));
-    r.kc = (float)(0.25 / (s->dx * s->dy));
-    r.ihx2 = (float)(1.0 / (s->dx * s->dx));
-    r.ihy2 = (float)(1.0 / (s->dy * s->dy));
-    r.no_reaction = (s->params.flags & GG_FLAG_NO_REACTION) ? 1 : 0;
+    r.dt = (float)dt;
+    r.D = (float)p.D;
+    r.delta = (float)p.delta;
+    r.rho = (float)p.rho;
+    r.c = (float)p.c;
+    r.kx = (float)(0.5 / (dx * dx));
+    r.ky = (float)(0.5 / (dy * dy));
+    r.kc = (float)(0.25 / (dx * dy));
+    r.ihx2 = (float)(1.0 / (dx * dx));
+    r.ihy2 = (float)(1.0 / (dy * dy));
+    r.Kx = (float)(p.D / (dx * dx));
+    r.Ky = (float)(p.D / (dy * dy));
+    r.hKx = (float)(0.5 * p.D / (dx * dx));
+    r.hKy = (float)(0.5 * p.D / (dy * dy));
+    r.no_reaction = (p.flags & GG_FLAG_NO_REACTION) ? 1 : 0;
     return r;
 }
+
+Rates32 rates32(const gg_sim* s) { return make_rates32(s->dx, s->dy, s->dt, s->params); }
 
 Grid32 grid32(const gg_sim* s, int cur)
 {
@@ -64,7 +70,7 @@ Grid32 grid32(const gg_sim* s, int cur)
     const bool k = s->params.precision == GG_FP32_KAHAN;
     g.cu = k ? s->f32[cur][3] : nullptr; g.cv = k ? s->f32[cur][4] : nullptr; g.cw = k ? s->f32[cur][5] : nullptr;
     g.cuo = k ? s->f32[nxt][3] : nullptr; g.cvo = k ? s->f32[nxt][4] : nullptr; g.cwo = k ? s->f32[nxt][5] : nullptr;
-    g.a11 = s->a32[0]; g.a12 = s->a32[1]; g.a22 = s->a32[2];
+    g.ax = s->a32[0]; g.b = s->a32[1]; g.ay = s->a32[2];
     g.nx = s->nx; g.ny = s->ny; g.pitch = s->pitch;
     return g;
 }
@@ -360,7 +366,7 @@ int gg_create(const gg_grid* grid, const gg_params* params, const double* theta,
     for (int k = 0; k < 6 && e == cudaSuccess; ++k)
         e = cudaMemcpyAsync(ddst[k], hsrc[k], n * 8, cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
-        e = launch_coefficients(dth, dl1, dl2, s->nx, s->ny, fp64 ? (void*)s->a64[0] : (void*)s->a32[0],
+        e = launch_coefficients(dth, dl1, dl2, s->nx, s->ny, s->dx, s->dy, fp64 ? (void*)s->a64[0] : (void*)s->a32[0],
                                 fp64 ? (void*)s->a64[1] : (void*)s->a32[1], fp64 ? (void*)s->a64[2] : (void*)s->a32[2],
                                 s->pitch, fp64, s->counters, s->counters + 2, s->stream);
     const double* dstate[3] = {du0, dv0, dw0};
@@ -464,8 +470,14 @@ static void* field_ptr(gg_sim* s, int32_t field, bool& fp64)
         return fp64 ? (void*)s->f64[s->cur][field] : (void*)s->f32[s->cur][field];
     if (field >= GG_FIELD_COMP_U && field <= GG_FIELD_COMP_W) return kahan ? (void*)s->f32[s->cur][field] : nullptr;
     if (field >= GG_FIELD_A11 && field <= GG_FIELD_A22) {
+        // FP32 simulations keep face weights, not the cell entries: gg_read
+        // computes those from theta / lambda (field_ptr is not used for them)
         const int f = field - GG_FIELD_A11;
-        return fp64 ? (void*)s->a64[f] : (void*)s->a32[f];
+        return fp64 ? (void*)s->a64[f] : nullptr;
+    }
+    if (field >= GG_FIELD_FACE_X && field <= GG_FIELD_CROSS) {
+        static const int slot[3] = {0, 2, 1};  // face_x -> ax, face_y -> ay, cross -> b
+        return fp64 ? nullptr : (void*)s->a32[slot[field - GG_FIELD_FACE_X]];
     }
     return nullptr;
 }
@@ -490,11 +502,24 @@ int gg_read(gg_sim* s, int32_t field, void* dst, int32_t dst_on_device, int32_t 
     if (!dst) { s->last_error = "dst is NULL"; return GG_ERR_ARG; }
     bool fp64;
     void* src = field_ptr(s, field, fp64);
-    if (!src) { s->last_error = "field not available for this precision"; return GG_ERR_ARG; }
+    const bool cell_tensor = !fp64 && field >= GG_FIELD_A11 && field <= GG_FIELD_A22;
+    if (!src && !cell_tensor) { s->last_error = "field not available for this precision"; return GG_ERR_ARG; }
     const size_t n = (size_t)s->nx * s->ny;
     const size_t bytes = n * (dst_fp64 ? 8 : 4);
     cudaError_t e;
-    if (dst_on_device) {
+    if (cell_tensor) {
+        // the entries of eq. (2) in FP64 from theta / lambda, rounded to dst's type
+        void* d = dst;
+        if (!dst_on_device) {
+            int rc = ensure_staging(s);
+            if (rc) return rc;
+            d = s->staging;
+        }
+        e = launch_tensor_entry(s->tensor[0], s->tensor[1], s->tensor[2], n, field - GG_FIELD_A11, d,
+                                dst_fp64 != 0, s->stream);
+        if (e == cudaSuccess && !dst_on_device)
+            e = cudaMemcpyAsync(dst, s->staging, bytes, cudaMemcpyDeviceToHost, s->stream);
+    } else if (dst_on_device) {
         e = launch_pack(src, fp64, dst, dst_fp64 != 0, s->nx, s->ny, s->pitch, s->stream);
     } else {
         int rc = ensure_staging(s);
@@ -511,7 +536,7 @@ int gg_write(gg_sim* s, int32_t field, const void* src, int32_t src_on_device, i
 {
     if (!s) return GG_ERR_ARG;
     if (!src) { s->last_error = "src is NULL"; return GG_ERR_ARG; }
-    if (field > GG_FIELD_COMP_W) { s->last_error = "tensor fields are read-only"; return GG_ERR_ARG; }
+    if (field > GG_FIELD_COMP_W) { s->last_error = "tensor and coefficient fields are read-only"; return GG_ERR_ARG; }
     bool fp64;
     void* dstp = field_ptr(s, field, fp64);
     if (!dstp) { s->last_error = "field not available for this precision"; return GG_ERR_ARG; }

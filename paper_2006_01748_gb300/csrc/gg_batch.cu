@@ -178,16 +178,10 @@ void build_desc(gg_batch* b, std::vector<InstDesc>& desc, std::vector<int2> item
             g.cw = b->kahan ? h.f[p][5] : nullptr;
             g.cuo = b->kahan ? h.f[q][3] : nullptr; g.cvo = b->kahan ? h.f[q][4] : nullptr;
             g.cwo = b->kahan ? h.f[q][5] : nullptr;
-            g.a11 = h.a[0]; g.a12 = h.a[1]; g.a22 = h.a[2];
+            g.ax = h.a[0]; g.b = h.a[1]; g.ay = h.a[2];
             g.nx = h.nx; g.ny = h.ny; g.pitch = h.pitch;
         }
-        Rates32& r = d.r;
-        r.dt = (float)h.dt; r.D = (float)h.params.D; r.delta = (float)h.params.delta;
-        r.rho = (float)h.params.rho; r.c = (float)h.params.c;
-        r.kx = (float)(0.5 / (h.dx * h.dx)); r.ky = (float)(0.5 / (h.dy * h.dy));
-        r.kc = (float)(0.25 / (h.dx * h.dy));
-        r.ihx2 = (float)(1.0 / (h.dx * h.dx)); r.ihy2 = (float)(1.0 / (h.dy * h.dy));
-        r.no_reaction = (h.params.flags & GG_FLAG_NO_REACTION) ? 1 : 0;
+        d.r = make_rates32(h.dx, h.dy, h.dt, h.params);
         const int chunks = (h.ny + b->plan.by - 1) / b->plan.by;
         for (int v = 0; v < 2; ++v) {
             d.strips[v] = (h.nx + outs[v] - 1) / outs[v];

@@ -18,12 +18,18 @@ constexpr int kDiagStride = 16;    // doubles per diagnostics partial
 
 // Device-side description of one FP32 state on a pitched grid.  Row j of a
 // field starts at base + j * pitch; pitch is a multiple of 32 floats.
+// The tensor of eq. (2) enters the FP32 kernels through three coefficient
+// fields, built once per tissue in FP64 and rounded once:
+//   ax(i,j) = (a11(i,j) + a11(i+1,j)) / (2 dx^2)   east face, 0 on the last column
+//   ay(i,j) = (a22(i,j) + a22(i,j+1)) / (2 dy^2)   north face, 0 on the last row
+//   b(i,j)  = a12(i,j) / (4 dx dy)                 cell
+// (the face weights and the cross-term weight of Table 2).
 struct Grid32 {
     const float* u; const float* v; const float* w;
     const float* cu; const float* cv; const float* cw;   // null without Kahan
     float* uo; float* vo; float* wo;
     float* cuo; float* cvo; float* cwo;
-    const float* a11; const float* a12; const float* a22;
+    const float* ax; const float* b; const float* ay;
     int nx, ny, pitch;
 };
 
@@ -32,8 +38,11 @@ struct Rates32 {
     float dt, D, delta, rho, c;
     float kx, ky, kc;     // 0.5/dx^2, 0.5/dy^2, 0.25/(dx dy)
     float ihx2, ihy2;     // 1/dx^2, 1/dy^2
+    float Kx, Ky;         // D/dx^2, D/dy^2 (tumour face weights, D folded in)
+    float hKx, hKy;       // Kx/2, Ky/2
     int no_reaction;
 };
+Rates32 make_rates32(double dx, double dy, double dt, const gg_params& p);
 
 // Launch plan of the FP32 step.  kind 0: shared-memory wavefront (strips of
 // bx output columns plus a halo of `halo` columns on each side, chunks of by
@@ -77,14 +86,20 @@ struct Rates64 {
 };
 cudaError_t launch_step64(const Grid64& g, const Rates64& r, cudaStream_t s);
 
-// Coefficients of eq. (2) and validation counters.
+// Coefficients of eq. (2) and validation counters.  fp64: a11, a12, a22
+// per cell (pitched doubles) into c0, c1, c2; otherwise the FP32 coefficient
+// fields ax, b, ay of Grid32 into c0, c1, c2 (dx, dy used only then).
 // counters[0]: cells with lambda <= 0 or non-finite theta/lambda;
 // counters[1]: non-finite initial values; lmax_bits: max lambda_max as the
 // bit pattern of a non-negative double (atomicMax on unsigned long long).
 cudaError_t launch_coefficients(const double* theta, const double* l1, const double* l2, int nx, int ny,
-                                void* a11, void* a12, void* a22, int pitch, bool fp64,
+                                double dx, double dy, void* c0, void* c1, void* c2, int pitch, bool fp64,
                                 unsigned long long* counters, unsigned long long* lmax_bits,
                                 cudaStream_t s);
+// One entry of eq. (2) (which = 0: a11, 1: a12, 2: a22) per cell from dense
+// FP64 theta / lambda, into a dense buffer of n floats or doubles.
+cudaError_t launch_tensor_entry(const double* theta, const double* l1, const double* l2, size_t n, int which,
+                                void* dst, bool dst_fp64, cudaStream_t s);
 
 // Dense FP64 host-layout field -> pitched FP32/FP64 device field (counts
 // non-finite values into *nonfinite when it is not null).

@@ -69,10 +69,25 @@ __global__ void __launch_bounds__(256) step64_kernel(const Grid64 g, const Rates
 
 // ---------------------------------------------------------------- eq. (2)
 
-template <typename F>
+// A = R(theta) diag(L1, L2) R(theta)^T at one cell.
+__device__ __forceinline__ void tensor_at(double th, double L1, double L2, double& A11, double& A12, double& A22)
+{
+    double s, c;
+    sincos(th, &s, &c);
+    A11 = L1 * c * c + L2 * s * s;
+    A12 = (L1 - L2) * s * c;
+    A22 = L1 * s * s + L2 * c * c;
+}
+
+// FP64 kernels get a11, a12, a22 per cell.  FP32 kernels get the face
+// weights ax = (a11 + a11_east) kx, ay = (a22 + a22_north) ky (0 on the last
+// column / row, whose east / north face is a boundary face) and b = a12 kc,
+// computed in FP64 and rounded once.
+template <bool FACES, typename F>
 __global__ void coefficients_kernel(const double* __restrict__ theta, const double* __restrict__ l1,
-                                    const double* __restrict__ l2, int nx, int ny, F* a11, F* a12, F* a22,
-                                    int pitch, unsigned long long* counters, unsigned long long* lmax_bits)
+                                    const double* __restrict__ l2, int nx, int ny, double kx, double ky, double kc,
+                                    F* c0, F* c1, F* c2, int pitch, unsigned long long* counters,
+                                    unsigned long long* lmax_bits)
 {
     __shared__ double smax[32];
     __shared__ unsigned long long sbad[32];
@@ -83,16 +98,21 @@ __global__ void coefficients_kernel(const double* __restrict__ theta, const doub
         const int j = (int)(q / nx), i = (int)(q % nx);
         const double th = theta[q], L1 = l1[q], L2 = l2[q];
         if (!(isfinite(th) && isfinite(L1) && isfinite(L2)) || !(L1 > 0.0) || !(L2 > 0.0)) ++bad;
-        double s, c;
-        sincos(th, &s, &c);
-        // A = R(theta) diag(L1, L2) R(theta)^T
-        const double A11 = L1 * c * c + L2 * s * s;
-        const double A12 = (L1 - L2) * s * c;
-        const double A22 = L1 * s * s + L2 * c * c;
+        double A11, A12, A22;
+        tensor_at(th, L1, L2, A11, A12, A22);
         const size_t o = (size_t)j * pitch + i;
-        a11[o] = (F)A11;
-        a12[o] = (F)A12;
-        a22[o] = (F)A22;
+        if constexpr (FACES) {
+            double e11 = 0.0, e12 = 0.0, e22 = 0.0, n11 = 0.0, n12 = 0.0, n22 = 0.0;
+            if (i + 1 < nx) tensor_at(theta[q + 1], l1[q + 1], l2[q + 1], e11, e12, e22);
+            if (j + 1 < ny) tensor_at(theta[q + nx], l1[q + nx], l2[q + nx], n11, n12, n22);
+            c0[o] = (F)(i + 1 < nx ? (A11 + e11) * kx : 0.0);
+            c1[o] = (F)(A12 * kc);
+            c2[o] = (F)(j + 1 < ny ? (A22 + n22) * ky : 0.0);
+        } else {
+            c0[o] = (F)A11;
+            c1[o] = (F)A12;
+            c2[o] = (F)A22;
+        }
         const double h = 0.5 * (A11 - A22);
         const double e = 0.5 * (A11 + A22) + sqrt(h * h + A12 * A12);
         if (e > lmax) lmax = e;  // NaN never wins
@@ -289,18 +309,41 @@ cudaError_t launch_step64(const Grid64& g, const Rates64& r, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_coefficients(const double* theta, const double* l1, const double* l2, int nx, int ny, void* a11,
-                                void* a12, void* a22, int pitch, bool fp64, unsigned long long* counters,
-                                unsigned long long* lmax_bits, cudaStream_t s)
+cudaError_t launch_coefficients(const double* theta, const double* l1, const double* l2, int nx, int ny, double dx,
+                                double dy, void* c0, void* c1, void* c2, int pitch, bool fp64,
+                                unsigned long long* counters, unsigned long long* lmax_bits, cudaStream_t s)
 {
     const size_t n = (size_t)nx * ny;
     const int blocks = blocks_for(n, 256);
     if (fp64)
-        coefficients_kernel<double><<<blocks, 256, 0, s>>>(theta, l1, l2, nx, ny, (double*)a11, (double*)a12,
-                                                           (double*)a22, pitch, counters, lmax_bits);
+        coefficients_kernel<false, double><<<blocks, 256, 0, s>>>(theta, l1, l2, nx, ny, 0.0, 0.0, 0.0, (double*)c0,
+                                                                  (double*)c1, (double*)c2, pitch, counters,
+                                                                  lmax_bits);
     else
-        coefficients_kernel<float><<<blocks, 256, 0, s>>>(theta, l1, l2, nx, ny, (float*)a11, (float*)a12,
-                                                          (float*)a22, pitch, counters, lmax_bits);
+        coefficients_kernel<true, float><<<blocks, 256, 0, s>>>(theta, l1, l2, nx, ny, 0.5 / (dx * dx),
+                                                                0.5 / (dy * dy), 0.25 / (dx * dy), (float*)c0,
+                                                                (float*)c1, (float*)c2, pitch, counters, lmax_bits);
+    return cudaGetLastError();
+}
+
+template <typename F>
+__global__ void tensor_entry_kernel(const double* __restrict__ theta, const double* __restrict__ l1,
+                                    const double* __restrict__ l2, size_t n, int which, F* dst)
+{
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        double A[3];
+        tensor_at(theta[q], l1[q], l2[q], A[0], A[1], A[2]);
+        dst[q] = (F)A[which];
+    }
+}
+
+cudaError_t launch_tensor_entry(const double* theta, const double* l1, const double* l2, size_t n, int which,
+                                void* dst, bool dst_fp64, cudaStream_t s)
+{
+    if (which < 0 || which > 2) return cudaErrorInvalidValue;
+    const int blocks = blocks_for(n, 256);
+    if (dst_fp64) tensor_entry_kernel<double><<<blocks, 256, 0, s>>>(theta, l1, l2, n, which, (double*)dst);
+    else tensor_entry_kernel<float><<<blocks, 256, 0, s>>>(theta, l1, l2, n, which, (float*)dst);
     return cudaGetLastError();
 }
 

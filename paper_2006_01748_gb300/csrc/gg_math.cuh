@@ -2,20 +2,23 @@
 //
 // eq. (3) is evaluated from face fluxes (the flux form of Tables 1 and 2):
 //
-//   D1(V;U)_P = (h(P,E) - h(W,P)) + (h(P,N) - h(S,P)),
-//       h(L,R) = (1 - (U_L + U_R)/2) (V_R - V_L) / h^2           (Table 1)
-//   D2(W;A)_P = (Gx(P,E) - Gx(W,P)) + (Gy(P,N) - Gy(S,P)),
-//       Gx(L,R) = (a11_L + a11_R)/(2 dx^2) (W_R - W_L)
-//               + (a12_L ty_L + a12_R ty_R) / (4 dx dy)          (Table 2)
-//       ty = W_north - W_south at the same column, tx = W_east - W_west
-//       (mirror ghosts at the domain boundary), Gy likewise.
+//   D D1(V;U)_P = (h(P,E) - h(W,P)) + (h(P,N) - h(S,P)),
+//       h(L,R) = D/h^2 (1 - (U_L + U_R)/2) (V_R - V_L)              (Table 1)
+//   D2(W;A)_P = (G(P,E) - G(W,P)) + (G(P,N) - G(S,P)),
+//       G(L,R) = a_f (W_R - W_L) + (z_L + z_R)                      (Table 2)
+//       a_f = (a11_L + a11_R)/(2 dx^2) on x-faces, (a22_L + a22_R)/(2 dy^2)
+//       on y-faces (built once per tissue, Grid32::ax / ay), and
+//       z = a12/(4 dx dy) * t per cell with t the tangential difference:
+//       t = W_north - W_south on x-faces, W_east - W_west on y-faces
+//       (mirror ghosts at the domain boundary).
 //
-// A face on the domain boundary carries zero flux (Section 2): callers pass
-// 0 for it.  Every operation uses an explicit round-to-nearest intrinsic, so
-// that the compiler cannot contract or reorder it differently in different
-// kernels: a face computed once and shared (warp kernel) and the same face
-// computed from both sides (shared-memory kernel) give the same bits, and
-// every launch plan produces the same result.
+// D is folded into the tumour face weight, so h already carries the factor
+// D of eq. (3).  A face on the domain boundary carries zero flux (Section 2):
+// callers pass 0 for it.  Every operation uses an explicit round-to-nearest
+// intrinsic, so that the compiler cannot contract or reorder it differently
+// in different kernels: a face computed once and shared (warp kernel) and the
+// same face computed from both sides (shared-memory kernel) give the same
+// bits, and every launch plan produces the same result.
 #pragma once
 
 #include "gg_internal.cuh"
@@ -23,26 +26,20 @@
 namespace gg {
 namespace fvm {
 
-__device__ __forceinline__ float gx_face(const Rates32& k, float a11L, float a11R, float wL, float wR, float bL,
-                                         float tyL, float bR, float tyR)
+// Acid flux through a face from its weight a, the two cell values (west /
+// south first) and the two cells' cross terms.
+__device__ __forceinline__ float g_face(float a, float wL, float wR, float zL, float zR)
 {
-    const float n = __fmul_rn(__fmul_rn(__fadd_rn(a11L, a11R), __fsub_rn(wR, wL)), k.kx);
-    const float c = __fmaf_rn(bL, tyL, __fmul_rn(bR, tyR));
-    return __fmaf_rn(k.kc, c, n);
+    return __fmaf_rn(a, __fsub_rn(wR, wL), __fadd_rn(zL, zR));
 }
 
-__device__ __forceinline__ float gy_face(const Rates32& k, float a22S, float a22N, float wS, float wN, float bS,
-                                         float txS, float bN, float txN)
-{
-    const float n = __fmul_rn(__fmul_rn(__fadd_rn(a22S, a22N), __fsub_rn(wN, wS)), k.ky);
-    const float c = __fmaf_rn(bS, txS, __fmul_rn(bN, txN));
-    return __fmaf_rn(k.kc, c, n);
-}
+// Cross term of one cell: b = a12/(4 dx dy) times its tangential difference.
+__device__ __forceinline__ float cross(float b, float t) { return __fmul_rn(b, t); }
 
-__device__ __forceinline__ float h_face(float uL, float uR, float vL, float vR, float ih2)
+// Tumour flux through a face: (K - K/2 (U_L + U_R)) (V_R - V_L), K = D/h^2.
+__device__ __forceinline__ float h_face(float uL, float uR, float vL, float vR, float K, float hK)
 {
-    const float m = __fmaf_rn(-0.5f, __fadd_rn(uL, uR), 1.0f);
-    return __fmul_rn(__fmul_rn(m, __fsub_rn(vR, vL)), ih2);
+    return __fmul_rn(__fmaf_rn(-hK, __fadd_rn(uL, uR), K), __fsub_rn(vR, vL));
 }
 
 // Rates of eq. (3) from the four face fluxes of each operator.
@@ -50,16 +47,16 @@ __device__ __forceinline__ void rates_faces(const Rates32& k, float up, float vp
                                             float hN, float hS, float gE, float gW, float gN, float gS, float& fu,
                                             float& fv, float& fw)
 {
-    const float d1 = __fadd_rn(__fsub_rn(hE, hW), __fsub_rn(hN, hS));
+    const float d1 = __fadd_rn(__fsub_rn(hE, hW), __fsub_rn(hN, hS));  // D D1
     const float d2 = __fadd_rn(__fsub_rn(gE, gW), __fsub_rn(gN, gS));
     if (k.no_reaction) {
         fu = 0.0f;
-        fv = __fmul_rn(k.D, d1);
+        fv = d1;
         fw = d2;
     } else {
-        // U(1-U) - delta U W,  rho V(1-V) + D D1,  c (V-W) + D2
-        fu = __fmaf_rn(-k.delta, __fmul_rn(up, wp), __fmul_rn(up, __fsub_rn(1.0f, up)));
-        fv = __fmaf_rn(k.D, d1, __fmul_rn(__fmul_rn(k.rho, vp), __fsub_rn(1.0f, vp)));
+        // U((1-U) - delta W),  rho V (1-V) + D D1,  c (V-W) + D2
+        fu = __fmul_rn(up, __fmaf_rn(-k.delta, wp, __fsub_rn(1.0f, up)));
+        fv = __fmaf_rn(__fmul_rn(k.rho, vp), __fsub_rn(1.0f, vp), d1);
         fw = __fmaf_rn(k.c, __fsub_rn(vp, wp), d2);
     }
 }

@@ -28,7 +28,7 @@ namespace step32 {
 
 struct Rows {
     const float *uS, *uP, *uN, *vS, *vP, *vN, *wS, *wP, *wN;
-    const float *a11P, *a12S, *a12P, *a12N, *a22S, *a22P, *a22N;
+    const float *axP, *bS, *bP, *bN, *ayS, *ayP;
 };
 
 // Rates (fu, fv, fw) of eq. (3) at one cell from shared-memory rows.  lxW /
@@ -46,17 +46,22 @@ __device__ __forceinline__ void cell_rates(const Rows& R, const Rates32& k, int 
     wp = R.wP[lx];
     const float wE = R.wP[lxE], wW = R.wP[lxW], wN = R.wN[lx], wS = R.wS[lx];
     const float wNE = R.wN[lxE], wNW = R.wN[lxW], wSE = R.wS[lxE], wSW = R.wS[lxW];
-    const float tyP = __fsub_rn(wN, wS), tyE = __fsub_rn(wNE, wSE), tyW = __fsub_rn(wNW, wSW);
-    const float txP = __fsub_rn(wE, wW), txN = __fsub_rn(wNE, wNW), txS = __fsub_rn(wSE, wSW);
-    const float a11P = R.a11P[lx], bP = R.a12P[lx], a22P = R.a22P[lx];
-    const float gE = hasE ? fvm::gx_face(k, a11P, R.a11P[lxE], wp, wE, bP, tyP, R.a12P[lxE], tyE) : 0.0f;
-    const float gW = hasW ? fvm::gx_face(k, R.a11P[lxW], a11P, wW, wp, R.a12P[lxW], tyW, bP, tyP) : 0.0f;
-    const float gN = hasN ? fvm::gy_face(k, a22P, R.a22N[lx], wp, wN, bP, txP, R.a12N[lx], txN) : 0.0f;
-    const float gS = hasS ? fvm::gy_face(k, R.a22S[lx], a22P, wS, wp, R.a12S[lx], txS, bP, txP) : 0.0f;
-    const float hE = hasE ? fvm::h_face(up, R.uP[lxE], vp, R.vP[lxE], k.ihx2) : 0.0f;
-    const float hW = hasW ? fvm::h_face(R.uP[lxW], up, R.vP[lxW], vp, k.ihx2) : 0.0f;
-    const float hN = hasN ? fvm::h_face(up, R.uN[lx], vp, R.vN[lx], k.ihy2) : 0.0f;
-    const float hS = hasS ? fvm::h_face(R.uS[lx], up, R.vS[lx], vp, k.ihy2) : 0.0f;
+    // cross terms: x faces use t = W_N - W_S, y faces t = W_E - W_W
+    const float bP = R.bP[lx];
+    const float zxP = fvm::cross(bP, __fsub_rn(wN, wS));
+    const float zxE = fvm::cross(R.bP[lxE], __fsub_rn(wNE, wSE));
+    const float zxW = fvm::cross(R.bP[lxW], __fsub_rn(wNW, wSW));
+    const float zyP = fvm::cross(bP, __fsub_rn(wE, wW));
+    const float zyN = fvm::cross(R.bN[lx], __fsub_rn(wNE, wNW));
+    const float zyS = fvm::cross(R.bS[lx], __fsub_rn(wSE, wSW));
+    const float gE = hasE ? fvm::g_face(R.axP[lx], wp, wE, zxP, zxE) : 0.0f;
+    const float gW = hasW ? fvm::g_face(R.axP[lxW], wW, wp, zxW, zxP) : 0.0f;
+    const float gN = hasN ? fvm::g_face(R.ayP[lx], wp, wN, zyP, zyN) : 0.0f;
+    const float gS = hasS ? fvm::g_face(R.ayS[lx], wS, wp, zyS, zyP) : 0.0f;
+    const float hE = hasE ? fvm::h_face(up, R.uP[lxE], vp, R.vP[lxE], k.Kx, k.hKx) : 0.0f;
+    const float hW = hasW ? fvm::h_face(R.uP[lxW], up, R.vP[lxW], vp, k.Kx, k.hKx) : 0.0f;
+    const float hN = hasN ? fvm::h_face(up, R.uN[lx], vp, R.vN[lx], k.Ky, k.hKy) : 0.0f;
+    const float hS = hasS ? fvm::h_face(R.uS[lx], up, R.vS[lx], vp, k.Ky, k.hKy) : 0.0f;
     fvm::rates_faces(k, up, vp, wp, hE, hW, hN, hS, gE, gW, gN, gS, fu, fv, fw);
 }
 
@@ -124,9 +129,9 @@ __device__ __forceinline__ void tile_pass(const Grid32& g, const Rates32& k, con
                 pre[m][0] = ld_state<COHERENT>(g.u + o);
                 pre[m][1] = ld_state<COHERENT>(g.v + o);
                 pre[m][2] = ld_state<COHERENT>(g.w + o);
-                pre[m][3] = __ldg(g.a11 + o);
-                pre[m][4] = __ldg(g.a12 + o);
-                pre[m][5] = __ldg(g.a22 + o);
+                pre[m][3] = __ldg(g.ax + o);
+                pre[m][4] = __ldg(g.b + o);
+                pre[m][5] = __ldg(g.ay + o);
                 if constexpr (KAHAN) {
                     pre[m][6] = ld_state<COHERENT>(g.cu + o);
                     pre[m][7] = ld_state<COHERENT>(g.cv + o);
@@ -179,9 +184,9 @@ __device__ __forceinline__ void tile_pass(const Grid32& g, const Rates32& k, con
                 R.uS = ST(t - 1, 0, pS); R.uP = ST(t - 1, 0, pP); R.uN = ST(t - 1, 0, pN);
                 R.vS = ST(t - 1, 1, pS); R.vP = ST(t - 1, 1, pP); R.vN = ST(t - 1, 1, pN);
                 R.wS = ST(t - 1, 2, pS); R.wP = ST(t - 1, 2, pP); R.wN = ST(t - 1, 2, pN);
-                R.a11P = CF(0, cPs);
-                R.a12S = CF(1, cS); R.a12P = CF(1, cPs); R.a12N = CF(1, cN);
-                R.a22S = CF(2, cS); R.a22P = CF(2, cPs); R.a22N = CF(2, cN);
+                R.axP = CF(0, cPs);
+                R.bS = CF(1, cS); R.bP = CF(1, cPs); R.bN = CF(1, cN);
+                R.ayS = CF(2, cS); R.ayP = CF(2, cPs);
                 const int s2 = r % 2;
 #pragma unroll
                 for (int m = 0; m < MAXM; ++m) {

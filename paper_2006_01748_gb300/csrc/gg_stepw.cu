@@ -1,26 +1,36 @@
 // Launchers of the warp-register wavefront step (kernel body in gg_stepw.cuh).
+//
+// CTA size: for T >= 2 one warp per CTA.  The warps share nothing, and with
+// a 32-thread bound the compiler keeps the T = 3 Kahan kernel at 120
+// registers (T = 4 at 152) without spills, so that 17 (13) warps fit on an
+// SM; with 4-warp CTAs it allocated 135 (168, with spills) and the SM held
+// 12.  Measured on the 8192^2 tissue: T = 3 225 vs 183 G cell-steps/s.  The
+// T = 1 kernel (64 registers, short-lived warps) keeps 4-warp CTAs, which
+// measured 105 vs 96 G cell-steps/s.
 #include "gg_stepw.cuh"
 
 namespace gg {
 namespace {
 
+template <int T> constexpr int warps_per_cta() { return T == 1 ? 4 : 1; }
+
 template <int T, bool KAHAN>
-__global__ void __launch_bounds__(128) stepw_kernel(const Grid32 g, const Rates32 k, const int H, const int nstrips,
-                                                    const int nwarps)
+__global__ void __launch_bounds__(32 * warps_per_cta<T>()) stepw_kernel(const Grid32 g, const Rates32 k, const int H,
+                                                                        const int nstrips, const int nwarps)
 {
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int gw = blockIdx.x * warps_per_cta<T>() + (threadIdx.x >> 5);
     if (gw >= nwarps) return;  // whole warps only
     const int strip = gw % nstrips, chunk = gw / nstrips;
     stepw::warp_pass_any<T, KAHAN>(g, k, H, strip, chunk, lane);
 }
 
 template <int T, bool KAHAN>
-__global__ void __launch_bounds__(128) stepw_stash_kernel(const Grid32 g, const Rates32 k, const int H,
-                                                          const int nstrips, const int nwarps, const Stash32 st)
+__global__ void __launch_bounds__(32) stepw_stash_kernel(const Grid32 g, const Rates32 k, const int H,
+                                                         const int nstrips, const int nwarps, const Stash32 st)
 {
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x;
+    const int gw = blockIdx.x;
     if (gw >= nwarps) return;
     const int strip = gw % nstrips, chunk = gw / nstrips;
     stepw::warp_pass_any<T, KAHAN, false, true>(g, k, H, strip, chunk, lane, &st);
@@ -33,7 +43,7 @@ cudaError_t launch_ws(const Grid32& g, const Rates32& r, int H, const Stash32& s
     const int nstrips = (g.nx + OUT - 1) / OUT;
     const int nchunks = (g.ny + H - 1) / H;
     const int nwarps = nstrips * nchunks;
-    stepw_stash_kernel<T, KAHAN><<<(nwarps + 3) / 4, 128, 0, s>>>(g, r, H, nstrips, nwarps, st);
+    stepw_stash_kernel<T, KAHAN><<<nwarps, 32, 0, s>>>(g, r, H, nstrips, nwarps, st);
     return cudaGetLastError();
 }
 
@@ -44,8 +54,8 @@ cudaError_t launch_w(const Grid32& g, const Rates32& r, int H, cudaStream_t s)
     const int nstrips = (g.nx + OUT - 1) / OUT;
     const int nchunks = (g.ny + H - 1) / H;
     const int nwarps = nstrips * nchunks;
-    const int wpb = 4;
-    stepw_kernel<T, KAHAN><<<(nwarps + wpb - 1) / wpb, 32 * wpb, 0, s>>>(g, r, H, nstrips, nwarps);
+    constexpr int wpc = warps_per_cta<T>();
+    stepw_kernel<T, KAHAN><<<(nwarps + wpc - 1) / wpc, 32 * wpc, 0, s>>>(g, r, H, nstrips, nwarps);
     return cudaGetLastError();
 }
 

@@ -14,7 +14,10 @@
 // Each lane computes the east and north face fluxes of its cell once
 // (gg_math.cuh); the west face is the east face of the lane to the west (one
 // shuffle) and the south face is the north face the same level computed one
-// tick earlier (a register).  Level t is valid on lanes [t, 32 - t), so a
+// tick earlier (a register).  Row q + 1, which level t reads as its north
+// row at tick k, is its own row at tick k + 1: the east / west neighbours of
+// w and the y cross term of that row are kept from one tick to the next
+// instead of being exchanged again.  Level t is valid on lanes [t, 32 - t), so a
 // warp writes its 32 - 2T middle columns and neighbouring strips overlap by
 // 2T columns.  Warps that touch the west or east domain boundary run a
 // variant with the boundary conditions; interior warps skip them.
@@ -62,8 +65,9 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
     // windows of level t-1 used by level t, index t-1
     float sW[T], pU[T], pV[T], pW[T], nU[T], nV[T], nW[T];
     float cP[T][3], cN[T][3];
-    float cf[T + 1][3];  // [age][a11, a12, a22]; age a holds input row R - a
-    float carG[T + 1], carH[T + 1];
+    float cf[T + 1][3];  // [age][ax, b, ay]; age a holds input row R - a
+    float carG[T + 1], carH[T + 1];           // north faces of the previous tick
+    float carWE[T + 1], carZ[T + 1];          // east w and y cross term of the own row
 #pragma unroll
     for (int t = 0; t < T; ++t) {
         sW[t] = pU[t] = pV[t] = pW[t] = nU[t] = nV[t] = nW[t] = 0.0f;
@@ -73,7 +77,7 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
 #pragma unroll
     for (int a = 0; a <= T; ++a) {
         cf[a][0] = cf[a][1] = cf[a][2] = 0.0f;
-        carG[a] = carH[a] = 0.0f;
+        carG[a] = carH[a] = carWE[a] = carZ[a] = 0.0f;
     }
 
     auto fetch = [&](int r, float* in) {
@@ -82,9 +86,9 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
             in[0] = ld_state<COHERENT>(g.u + o);
             in[1] = ld_state<COHERENT>(g.v + o);
             in[2] = ld_state<COHERENT>(g.w + o);
-            in[3] = __ldg(g.a11 + o);
-            in[4] = __ldg(g.a12 + o);
-            in[5] = __ldg(g.a22 + o);
+            in[3] = __ldg(g.ax + o);
+            in[4] = __ldg(g.b + o);
+            in[5] = __ldg(g.ay + o);
             if constexpr (KAHAN) {
                 in[6] = ld_state<COHERENT>(g.cu + o);
                 in[7] = ld_state<COHERENT>(g.cv + o);
@@ -124,24 +128,30 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
             const bool hasS = YEDGE ? q > 0 : true, hasN = YEDGE ? q + 1 < ny : true;
             const float uP = pU[t - 1], vP = pV[t - 1], wP = pW[t - 1];
             const float uN = nU[t - 1], vN = nV[t - 1], wN = nW[t - 1];
-            const float a11P = cf[t][0], bP = cf[t][1], a22P = cf[t][2];
-            const float bN = cf[t - 1][1], a22N = cf[t - 1][2];
-            const float tyP = __fsub_rn(hasN ? wN : wP, hasS ? sW[t - 1] : wP);
-            float uE = from_east(uP), vE = from_east(vP), wE = from_east(wP), wW = from_west(wP);
+            const float axP = cf[t][0], bP = cf[t][1], ayP = cf[t][2];
+            const float bN = cf[t - 1][1];
+            // x cross term of the own row (tangential difference mirrored at
+            // the south / north boundary), shared with the west neighbour
+            const float zxP = fvm::cross(bP, __fsub_rn(hasN ? wN : wP, hasS ? sW[t - 1] : wP));
+            float uE = from_east(uP), vE = from_east(vP), zxE = from_east(zxP);
             float wNE = from_east(wN), wNW = from_west(wN);
-            float a11E = from_east(a11P), bE = from_east(bP), tyE = from_east(tyP);
             if constexpr (EDGE) {
-                if (!hasE) { uE = uP; vE = vP; wE = wP; wNE = wN; a11E = a11P; bE = bP; tyE = tyP; }
-                if (!hasW) { wW = wP; wNW = wN; }
+                if (!hasE) { uE = uP; vE = vP; wNE = wN; }
+                if (!hasW) wNW = wN;
             }
-            const float txP = __fsub_rn(wE, wW), txN = __fsub_rn(wNE, wNW);
-            float gE = fvm::gx_face(k, a11P, a11E, wP, wE, bP, tyP, bE, tyE);
-            float hE = fvm::h_face(uP, uE, vP, vE, k.ihx2);
+            // east w of the own row: the north row's of the last tick
+            const float wE = carWE[t];
+            carWE[t] = wNE;
+            // y cross terms of the own row (last tick's north row) and the north row
+            const float zyP = carZ[t], zyN = fvm::cross(bN, __fsub_rn(wNE, wNW));
+            carZ[t] = zyN;
+            float gE = fvm::g_face(axP, wP, wE, zxP, zxE);
+            float hE = fvm::h_face(uP, uE, vP, vE, k.Kx, k.hKx);
             if constexpr (EDGE) {
                 if (!hasE) { gE = 0.0f; hE = 0.0f; }
             }
-            const float gN = hasN ? fvm::gy_face(k, a22P, a22N, wP, wN, bP, txP, bN, txN) : 0.0f;
-            const float hN = hasN ? fvm::h_face(uP, uN, vP, vN, k.ihy2) : 0.0f;
+            const float gN = hasN ? fvm::g_face(ayP, wP, wN, zyP, zyN) : 0.0f;
+            const float hN = hasN ? fvm::h_face(uP, uN, vP, vN, k.Ky, k.hKy) : 0.0f;
             float gW = from_west(gE), hW = from_west(hE);
             if constexpr (EDGE) {
                 if (!hasW) { gW = 0.0f; hW = 0.0f; }

@@ -32,7 +32,8 @@ GG_FP32 = 1
 GG_FP32_KAHAN = 2
 PRECISIONS = {"fp64": GG_FP64_PLAIN, "fp64_plain": GG_FP64_PLAIN, "fp32": GG_FP32, "fp32_kahan": GG_FP32_KAHAN}
 
-FIELDS = {"u": 0, "v": 1, "w": 2, "comp_u": 3, "comp_v": 4, "comp_w": 5, "a11": 6, "a12": 7, "a22": 8}
+FIELDS = {"u": 0, "v": 1, "w": 2, "comp_u": 3, "comp_v": 4, "comp_w": 5, "a11": 6, "a12": 7, "a22": 8,
+          "face_x": 9, "face_y": 10, "cross": 11}
 
 GG_FLAG_NO_REACTION = 1
 GG_FLAG_ALLOW_UNSTABLE = 2
