@@ -38,24 +38,28 @@ using namespace gg;
 
 namespace {
 
-// Geometry of the warp-marching adjoint launch: 30 written columns per warp,
-// chunks of adj_chunk() rows sized for about 20 warps per SM (152 SMs; the
-// kernel is bounded to 5 CTAs of 4 warps per SM).
+// Geometry of the warp-marching adjoint launches.  A grid of strips x chunks
+// warps runs in waves of `cap` resident warps (152 SMs times the warps per SM
+// that the launch bounds guarantee).  The chunk height is chosen so that the
+// grid fills a whole number of waves where it can: a grid of one wave plus a
+// few CTAs takes about two warp lifetimes.
+inline int wave_chunk(int strips, int ny, int cap, int hmax)
+{
+    constexpr int hmin = 8;
+    if (strips > cap) return std::min(hmax, std::max(hmin, ny));
+    const int per_wave = cap / strips;  // chunk rows of warps per wave
+    const int waves = std::max(1, (ny + per_wave * hmax - 1) / (per_wave * hmax));
+    const int nch = waves * per_wave;
+    return std::min(hmax, std::max(hmin, (ny + nch - 1) / nch));
+}
+// Single step: 30 written columns per warp, 5 CTAs of 4 warps per SM.
 constexpr int kAdjOut = 30;
 inline int adj_strips(int nx) { return (nx + kAdjOut - 1) / kAdjOut; }
-inline int adj_chunk(int nx, int ny)
-{
-    const int chunks = std::max(1, (20 * 152 + adj_strips(nx) - 1) / adj_strips(nx));
-    return std::min(128, std::max(8, (ny + chunks - 1) / chunks));
-}
+inline int adj_chunk(int nx, int ny) { return wave_chunk(adj_strips(nx), ny, 20 * 152, 128); }
 inline int adj_warps(int nx, int ny) { const int H = adj_chunk(nx, ny); return adj_strips(nx) * ((ny + H - 1) / H); }
-// The two-step kernel writes 28 columns per warp and runs 4 CTAs per SM.
+// Two steps: 28 written columns per warp, 4 CTAs of 4 warps per SM.
 inline int adj2_strips(int nx) { return (nx + 27) / 28; }
-inline int adj2_chunk(int nx, int ny)
-{
-    const int chunks = std::max(1, (16 * 152 + adj2_strips(nx) - 1) / adj2_strips(nx));
-    return std::min(128, std::max(8, (ny + chunks - 1) / chunks));
-}
+inline int adj2_chunk(int nx, int ny) { return wave_chunk(adj2_strips(nx), ny, 16 * 152, 128); }
 inline int adj2_warps(int nx, int ny) { const int H = adj2_chunk(nx, ny); return adj2_strips(nx) * ((ny + H - 1) / H); }
 constexpr int kFlushEvery = 32;  // FP32 per-cell gradient sums are folded into FP64 this often
 
@@ -82,7 +86,8 @@ __device__ __forceinline__ float from_west(float x) { return __shfl_up_sync(kFul
 __device__ __forceinline__ float from_east(float x) { return __shfl_down_sync(kFull, x, 1); }
 
 // One row of the inputs of an adjoint step at one column: the fields read on
-// rows q-1, q, q+1 (AdjRow) and those read on row q only (AdjOwn).
+// rows q and q+1 (AdjRow; of row q-1 only w is read) and those read on row q
+// only (AdjOwn).
 struct AdjRow {
     float u, v, w, lv, lw, clv, clw, b, ay;
 };
@@ -97,62 +102,83 @@ struct AdjOut {
     float s_delta, s_rho, s_D, s_c;
 };
 
-// One adjoint step at row q of one lane, from the rows S (q-1), P (q), N (q+1)
-// of lam^{k+1} and X^k and the own-row fields lu, clu and ax (east-face
-// weight).  All lanes of the warp call it (it shuffles).
+// What one adjoint level passes from row q-1 to row q.  The level reads row
+// q+1 as its north row when it processes row q; at the next tick that row
+// is its own row.  So the x-face differences of lamW and the cross sums of
+// a row are computed once, when it is the north row, and every south-face
+// term of row q is the north-face term of row q-1 (of equal value, or of
+// opposite sign where the difference changes direction: it is kept with the
+// sign of the north face and subtracted).
+struct AdjCarry {
+    float LxE = 0.f, LxW = 0.f;  // lamW differences across the east / west faces of row q
+    float Sx = 0.f, SxS = 0.f;   // b (LxE + LxW) of rows q and q-1
+    float Ly = 0.f;              // lamW difference across the north face of row q-1
+    float h = 0.f, f = 0.f, e = 0.f, g = 0.f, qq = 0.f;  // north-face terms of row q-1 (below)
+};
+
+// One adjoint step at row q of one lane, from the state and lam of rows P (q)
+// and N (q+1), w of row q-1 and the own-row fields lu, clu and ax (east-face
+// weight), with the carry c of row q-1 (updated for row q+1).  All lanes of
+// the warp call it (it shuffles).  Face terms, each with the factor 1/h^2 of
+// its direction: with m = 1 - (U_P + U_nb)/2, dv = V_nb - V_P, dl the
+// compensated difference of lamV (neighbour minus own),
+//   h = m dv (D1 of V),  f = m dl (D1^T of lamV),  e = dv dl (dD1/dU),
+// the east / north terms are computed here, the west ones are the west
+// lane's east ones and the south ones the carried north ones of row q-1:
+//   D1 = (hE - hW) + (hN - hS),  D1^T = (fE - fW) + (fN - fS),
+//   dD1/dU = (eE + eW + eN + eS) / 2.
 template <bool KAHAN, bool EDGE, bool YEDGE = true>
-__device__ __forceinline__ AdjOut adj_level(const Rates32& k, const AdjRow& S, const AdjRow& P, const AdjRow& N,
-                                            float lu, float clu, float ax, bool hasW, bool hasE, bool hasS_,
-                                            bool hasN_)
+__device__ __forceinline__ AdjOut adj_level(const Rates32& k, float Sw, const AdjRow& P, const AdjRow& N, float lu,
+                                            float clu, float ax, bool hasW, bool hasE, bool hasS_, bool hasN_,
+                                            AdjCarry& c)
 {
     // interior chunks (YEDGE false) have both the south and the north face
     const bool hasS = YEDGE ? hasS_ : true, hasN = YEDGE ? hasN_ : true;
     // compensated difference of lam between two (value, Kahan term) pairs
     auto dW = [](float la, float ca, float lb, float cb) { return __fsub_rn(__fsub_rn(la, lb), __fsub_rn(ca, cb)); };
-    // face differences of lamW on rows S, P, N (0 on boundary faces)
-    auto lx_e = [&](const AdjRow& X) {
-        float le = from_east(X.lw), ce = from_east(X.clw);
-        const float d = dW(X.lw, X.clw, le, ce);
-        return hasE ? d : 0.0f;
-    };
-    const float LxE_P = lx_e(P), LxE_N = lx_e(N), LxE_S = lx_e(S);
-    float LxW_P = from_west(LxE_P), LxW_N = from_west(LxE_N), LxW_S = from_west(LxE_S);
-    if (EDGE && !hasW) { LxW_P = LxW_N = LxW_S = 0.0f; }
+    // x-face differences of lamW on the north row (0 on boundary faces)
+    const float lwE = from_east(N.lw), cwE = from_east(N.clw);
+    const float LxE_N = hasE ? dW(N.lw, N.clw, lwE, cwE) : 0.0f;
+    float LxW_N = from_west(LxE_N);
+    if (EDGE && !hasW) LxW_N = 0.0f;
+    const float LxE_P = c.LxE, LxW_P = c.LxW;
     const float LyN = hasN ? dW(P.lw, P.clw, N.lw, N.clw) : 0.0f;
-    const float LyS = hasS ? dW(S.lw, S.clw, P.lw, P.clw) : 0.0f;
+    const float LyS = hasS ? c.Ly : 0.0f;
     // transpose of the a12 cross terms (mirrored central differences; b
     // carries the factor 1/(4 dx dy))
-    const float SxP = P.b * (LxE_P + LxW_P), SxN = N.b * (LxE_N + LxW_N), SxS = S.b * (LxE_S + LxW_S);
+    const float SxN = N.b * (LxE_N + LxW_N), SxP = c.Sx, SxS = c.SxS;
     const float SyP = P.b * (LyN + LyS);
     float SyE = from_east(SyP), SyW = from_west(SyP);
     const float Ty = (hasS ? SxS : 0.0f) - (hasN ? SxN : 0.0f) + SxP * ((hasN ? 0.0f : 1.0f) - (hasS ? 0.0f : 1.0f));
     float Tx;
     if (EDGE) Tx = (hasW ? SyW : 0.0f) - (hasE ? SyE : 0.0f) + SyP * ((hasE ? 0.0f : 1.0f) - (hasW ? 0.0f : 1.0f));
     else Tx = SyW - SyE;
-    // face weights: east ax, west = the west lane's ax, north P.ay, south
-    // S.ay (a boundary face has L = 0, so its weight does not matter)
+    // face weights: east ax, west = the west lane's ax, north P.ay, south the
+    // carried product of row q-1 (a boundary face has L = 0)
     const float axW = from_west(ax);
-    const float D2T = (ax * (-LxE_P) + axW * LxW_P) + (P.ay * (-LyN) + S.ay * LyS) + (Tx + Ty);
+    const float gN = P.ay * LyN;
+    const float D2T = (ax * (-LxE_P) + axW * LxW_P) + ((hasS ? c.g : 0.0f) - gN) + (Tx + Ty);
 
     // state and lamV neighbourhood (mirrored at the boundary)
-    float uE = from_east(P.u), uW = from_west(P.u), vE = from_east(P.v), vW = from_west(P.v);
-    float wE = from_east(P.w), wW = from_west(P.w);
-    float lvE = from_east(P.lv), lvW = from_west(P.lv), cvE = from_east(P.clv), cvW = from_west(P.clv);
+    float uE = from_east(P.u), vE = from_east(P.v), wE = from_east(P.w), wW = from_west(P.w);
+    float lvE = from_east(P.lv), cvE = from_east(P.clv);
     if (EDGE) {
         if (!hasE) { uE = P.u; vE = P.v; wE = P.w; lvE = P.lv; cvE = P.clv; }
-        if (!hasW) { uW = P.u; vW = P.v; wW = P.w; lvW = P.lv; cvW = P.clv; }
+        if (!hasW) wW = P.w;
     }
-    const float uN = hasN ? N.u : P.u, uS = hasS ? S.u : P.u;
-    const float vN = hasN ? N.v : P.v, vS = hasS ? S.v : P.v;
-    const float wN = hasN ? N.w : P.w, wS = hasS ? S.w : P.w;
-    const float dlE = dW(lvE, cvE, P.lv, P.clv), dlW = dW(lvW, cvW, P.lv, P.clv);
-    const float dlN = hasN ? dW(N.lv, N.clv, P.lv, P.clv) : 0.0f, dlS = hasS ? dW(S.lv, S.clv, P.lv, P.clv) : 0.0f;
-    const float mE = 1.0f - 0.5f * (P.u + uE), mW = 1.0f - 0.5f * (P.u + uW);
-    const float mN = 1.0f - 0.5f * (P.u + uN), mS = 1.0f - 0.5f * (P.u + uS);
-    const float dvE = vE - P.v, dvW = vW - P.v, dvN = vN - P.v, dvS = vS - P.v;
-    const float d1 = (mE * dvE + mW * dvW) * k.ihx2 + (mN * dvN + mS * dvS) * k.ihy2;
-    const float d1T = (mE * dlE + mW * dlW) * k.ihx2 + (mN * dlN + mS * dlS) * k.ihy2;
-    const float dU = 0.5f * ((dvE * dlE + dvW * dlW) * k.ihx2 + (dvN * dlN + dvS * dlS) * k.ihy2);
+    const float uN = hasN ? N.u : P.u, vN = hasN ? N.v : P.v, wN = hasN ? N.w : P.w;
+    const float wS = hasS ? Sw : P.w;
+    const float mE = 1.0f - 0.5f * (P.u + uE), mN = 1.0f - 0.5f * (P.u + uN);
+    const float dvE = (vE - P.v) * k.ihx2, dvN = (vN - P.v) * k.ihy2;
+    const float dlE = dW(lvE, cvE, P.lv, P.clv), dlN = hasN ? dW(N.lv, N.clv, P.lv, P.clv) : 0.0f;
+    const float hE = mE * dvE, fE = mE * dlE * k.ihx2, eE = dvE * dlE;
+    const float hN = mN * dvN, fN = mN * dlN * k.ihy2, eN = dvN * dlN;
+    float hW = from_west(hE), fW = from_west(fE), eW = from_west(eE);
+    if (EDGE && !hasW) { hW = 0.0f; fW = 0.0f; eW = 0.0f; }
+    const float hS = hasS ? c.h : 0.0f, fS = hasS ? c.f : 0.0f, eS = hasS ? c.e : 0.0f;
+    const float d1 = (hE - hW) + (hN - hS);
+    const float d1T = (fE - fW) + (fN - fS);
+    const float dU = 0.5f * ((eE + eW) + (eN + eS));
 
     float fu, fvv, fw;
     AdjOut o;
@@ -180,9 +206,15 @@ __device__ __forceinline__ AdjOut adj_level(const Rates32& k, const AdjRow& S, c
         o.lw = P.lw + k.dt * fw;
         o.clu = o.clv = o.clw = 0.0f;
     }
+    const float qN = (wN - P.w) * LyN;
     o.d11 = k.dt * (((wE - P.w) * LxE_P + (P.w - wW) * LxW_P) * k.kx);
-    o.d22 = k.dt * (((wN - P.w) * LyN + (P.w - wS) * LyS) * k.ky);
+    o.d22 = k.dt * ((qN + (hasS ? c.qq : 0.0f)) * k.ky);
     o.d12 = k.dt * (((LxE_P + LxW_P) * (wN - wS) + (LyN + LyS) * (wE - wW)) * k.kc);
+    // row q becomes row q-1 of the next tick
+    c.LxE = LxE_N; c.LxW = LxW_N;
+    c.SxS = SxP; c.Sx = SxN;
+    c.Ly = LyN;
+    c.h = hN; c.f = fN; c.e = eN; c.g = gN; c.qq = qN;
     return o;
 }
 
@@ -236,9 +268,11 @@ __device__ __forceinline__ void load_row(const float* u, const float* v, const f
 }
 
 // Adjoint step as a warp march: the warp owns 32 columns (30 written) and a
-// chunk of H rows, keeps rows q-1, q, q+1 of its inputs in registers (window
-// rows fetched two ahead, own-row fields one ahead) and takes east / west
-// values by shuffle.
+// chunk of H rows, keeps rows q, q+1 (and w of q-1) of its inputs in
+// registers (window rows fetched two ahead, own-row fields one ahead) and
+// takes east / west values by shuffle.  The march starts two rows above the
+// chunk (not above row -1), so that the carry of the first written row is
+// complete.
 template <bool KAHAN, bool EDGE, bool YEDGE>
 __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, const int H, const int strip,
                                          const int chunk, const int lane, double* part)
@@ -250,6 +284,7 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
     const bool outc = ind && lane >= 1 && lane < 31;
     const int ys = chunk * H;
     const int ye = min(ny, ys + H);
+    const int q0 = max(-1, ys - 2);
     auto load = [&](int r, AdjRow& x) {
         load_row<KAHAN>(a.u, a.v, a.w, a.lv, a.lw, a.clv, a.clw, a.b, a.ay, ind && r >= 0 && r < ny,
                         (size_t)r * pitch + gx, x);
@@ -266,20 +301,21 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
         }
     };
     RateSums sums;
-    AdjRow S, P, N, nxt;
+    AdjCarry cy;
+    AdjRow P, N, nxt;
     AdjOwn PO, NO;
-    load(ys - 1, S);
-    load(ys, P);
-    load(ys + 1, N);
-    load(ys + 2, nxt);
-    load_own(ys, PO);
-    for (int q = ys; q < ye; ++q) {
+    float Sw = (ind && q0 - 1 >= 0) ? __ldg(a.w + (size_t)(q0 - 1) * pitch + gx) : 0.0f;
+    load(q0, P);
+    load(q0 + 1, N);
+    load(q0 + 2, nxt);
+    load_own(q0, PO);
+    for (int q = q0; q < ye; ++q) {
         AdjRow nn;
         load(q + 3, nn);
         load_own(q + 1, NO);
-        const AdjOut o = adj_level<KAHAN, EDGE, YEDGE>(k, S, P, N, PO.lu, PO.clu, PO.ax, hasW, hasE, q > 0,
-                                                       q + 1 < ny);
-        if (outc) {
+        const AdjOut o = adj_level<KAHAN, EDGE, YEDGE>(k, Sw, P, N, PO.lu, PO.clu, PO.ax, hasW, hasE, q > 0,
+                                                       q + 1 < ny, cy);
+        if (q >= ys && outc) {
             const size_t off = (size_t)q * pitch + gx;
             sums.add_all(o);
             a.luo[off] = o.lu; a.lvo[off] = o.lv; a.lwo[off] = o.lw;
@@ -288,7 +324,7 @@ __device__ __forceinline__ void adj_warp(const AdjArgs& a, const Rates32& k, con
             a.g12[off] = PO.g12 + o.d12;
             a.g22[off] = PO.g22 + o.d22;
         }
-        S = P;
+        Sw = P.w;
         P = N;
         N = nxt;
         nxt = nn;
@@ -368,58 +404,68 @@ __device__ __forceinline__ void adj2_warp(const AdjArgs2& a, const Rates32& k, c
         }
     };
     RateSums sums;
-    // level-1 window (rows r-2, r-1, r) with own fields of row r-1 / r
-    AdjRow S1, P1, N1;
+    // Level 1 computes row r - 1 at tick r, level 2 row r - 2; each has its
+    // own carry.  Before the first written rows each level passes over two
+    // rows (from lo0), which completes its carry (at the top of the domain
+    // the missing south faces need none).
+    AdjCarry c1, c2;
+    // level-1 window: rows r-1 (P1), r (N1), w of r-2
+    AdjRow P1{}, N1{};
+    float S1w = 0.f;
     float luP = 0.f, cluP = 0.f, axP = 0.f, luN = 0.f, cluN = 0.f, axN = 0.f;
-    // level-2 window: lam^{k+1} rows and X^k rows (r-3, r-2, r-1), tensor rows via level 1's window history
-    AdjRow S2, P2, N2;
+    // level-2 window: lam^{k+1} and X^k of rows r-2 (P2), r-1 (N2), w of r-3
+    AdjRow P2{}, N2{};
+    float S2w = 0.f;
     float d11c = 0.f, d12c = 0.f, d22c = 0.f;      // level-1 gradient increments of level 2's row
-    float x0u[3] = {0.f, 0.f, 0.f}, x0v[3] = {0.f, 0.f, 0.f}, x0w[3] = {0.f, 0.f, 0.f};
-    S1 = P1 = N1 = AdjRow{};
-    S2 = P2 = N2 = AdjRow{};
-    // prefetch the first input rows
+    // prefetch the first level-1 input row
     AdjRow in1;
-    float inlu, inclu, inax, in0u, in0v, in0w;
+    float inlu, inclu, inax;
     load1(lo0, in1, inlu, inclu, inax);
-    load0(lo0 - 1, in0u, in0v, in0w);
     float lu1prev = 0.f, clu1prev = 0.f, axprev = 0.f;  // level-1 outputs of the previous tick
     AdjOut prev1{};
     bool prev_own = false;
     for (int tk = 0; tk < nticks; ++tk) {
         const int r = lo0 + tk;
         // input row r enters level 1's window; X^k row r - 1 enters level 2's
-        S1 = P1; P1 = N1; N1 = in1;
+        S1w = P1.w; P1 = N1; N1 = in1;
         luP = luN; cluP = cluN; axP = axN;
         luN = inlu; cluN = inclu; axN = inax;
-        x0u[0] = x0u[1]; x0u[1] = x0u[2]; x0u[2] = in0u;
-        x0v[0] = x0v[1]; x0v[1] = x0v[2]; x0v[2] = in0v;
-        x0w[0] = x0w[1]; x0w[1] = x0w[2]; x0w[2] = in0w;
+        // loads issued here are used after level 1 (X^k of row r - 1) and
+        // after level 2 (the gradient sums of row r - 2); the next level-1
+        // row is used at the next tick
+        float x0u, x0v, x0w;
+        load0(r - 1, x0u, x0v, x0w);
+        const int q2 = r - 2;
+        const bool own2 = q2 >= ys && q2 < ye && outc;
+        float g11 = 0.f, g12 = 0.f, g22 = 0.f;
+        if (own2) {
+            const size_t off = (size_t)q2 * pitch + gx;
+            g11 = __ldg(a.g11 + off); g12 = __ldg(a.g12 + off); g22 = __ldg(a.g22 + off);
+        }
         load1(r + 1, in1, inlu, inclu, inax);
-        load0(r, in0u, in0v, in0w);
         // level 1: row q1 = r - 1
         const int q1 = r - 1;
-        const AdjOut o1 = adj_level<KAHAN, EDGE, YEDGE>(k, S1, P1, N1, luP, cluP, axP, hasW, hasE, q1 > 0,
-                                                        q1 + 1 < ny);
-        const bool own1 = q1 >= ys && q1 < ye;
+        const AdjOut o1 = adj_level<KAHAN, EDGE, YEDGE>(k, S1w, P1, N1, luP, cluP, axP, hasW, hasE, q1 > 0,
+                                                        q1 + 1 < ny, c1);
+        const bool own1 = q1 >= ys && q1 < ye;  // level 1's rate terms count on the chunk's rows
         // level-1 lam^{k+1} row q1 enters level 2's window (with X^k row q1 and the tensor of row q1)
         AdjRow nw;
-        nw.u = x0u[2]; nw.v = x0v[2]; nw.w = x0w[2];
+        nw.u = x0u; nw.v = x0v; nw.w = x0w;
         nw.lv = o1.lv; nw.clv = o1.clv; nw.lw = o1.lw; nw.clw = o1.clw;
         nw.b = P1.b; nw.ay = P1.ay;
-        S2 = P2; P2 = N2; N2 = nw;
+        S2w = P2.w; P2 = N2; N2 = nw;
         // level 2: row q2 = r - 2, own fields from level 1's previous output
-        const int q2 = r - 2;
-        const AdjOut o2 = adj_level<KAHAN, EDGE, YEDGE>(k, S2, P2, N2, lu1prev, clu1prev, axprev, hasW, hasE,
-                                                        q2 > 0, q2 + 1 < ny);
-        if (q2 >= ys && q2 < ye && outc) {
+        const AdjOut o2 = adj_level<KAHAN, EDGE, YEDGE>(k, S2w, P2, N2, lu1prev, clu1prev, axprev, hasW, hasE,
+                                                        q2 > 0, q2 + 1 < ny, c2);
+        if (own2) {
             const size_t off = (size_t)q2 * pitch + gx;
             sums.add_all(o2);
             if (prev_own) sums.add_all(prev1);
             a.luo[off] = o2.lu; a.lvo[off] = o2.lv; a.lwo[off] = o2.lw;
             if (KAHAN) { a.cluo[off] = o2.clu; a.clvo[off] = o2.clv; a.clwo[off] = o2.clw; }
-            a.g11[off] = __ldg(a.g11 + off) + (d11c + o2.d11);
-            a.g12[off] = __ldg(a.g12 + off) + (d12c + o2.d12);
-            a.g22[off] = __ldg(a.g22 + off) + (d22c + o2.d22);
+            a.g11[off] = g11 + (d11c + o2.d11);
+            a.g12[off] = g12 + (d12c + o2.d12);
+            a.g22[off] = g22 + (d22c + o2.d22);
         }
         // level 1's row q1 becomes level 2's row at the next tick
         lu1prev = o1.lu; clu1prev = o1.clu; axprev = axP;

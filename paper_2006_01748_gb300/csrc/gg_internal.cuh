@@ -56,6 +56,9 @@ struct Plan32 {
 
 size_t step32_smem_bytes(const Plan32& p, bool kahan);
 cudaError_t launch_stepw(const Grid32& g, const Rates32& r, int H, int T, bool kahan, cudaStream_t s);
+// Warps of the warp-register kernel with T steps per pass that the device
+// holds at once (one wave); 0 if the occupancy query fails.
+int stepw_wave_warps(int T, bool kahan);
 
 // Destinations of the intermediate time levels of a pass (level t = 1..T-1
 // writes u, v, w of step s0 + t to u[t-1], v[t-1], w[t-1]); used to

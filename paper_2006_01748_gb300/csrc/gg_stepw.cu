@@ -59,7 +59,32 @@ cudaError_t launch_w(const Grid32& g, const Rates32& r, int H, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <int T, bool KAHAN>
+int wave_warps_T()
+{
+    constexpr int wpc = warps_per_cta<T>();
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stepw_kernel<T, KAHAN>, 32 * wpc, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * wpc * sms;
+}
+
 }  // namespace
+
+int stepw_wave_warps(int T, bool kahan)
+{
+    switch (T) {
+        case 1: return kahan ? wave_warps_T<1, true>() : wave_warps_T<1, false>();
+        case 2: return kahan ? wave_warps_T<2, true>() : wave_warps_T<2, false>();
+        case 3: return kahan ? wave_warps_T<3, true>() : wave_warps_T<3, false>();
+        case 4: return kahan ? wave_warps_T<4, true>() : wave_warps_T<4, false>();
+        default: return 0;
+    }
+}
 
 cudaError_t launch_stepw(const Grid32& g, const Rates32& r, int H, int T, bool kahan, cudaStream_t s)
 {

@@ -239,7 +239,18 @@ def test_tensor_entries_match_oracle():
             assert np.max(np.abs(sim.read(f) - r)) <= 1e-15
     with gg.GGSim.from_problem(p, precision="fp32") as sim:
         for f, r in zip(("a11", "a12", "a22"), a):
-            assert np.max(np.abs(sim.read(f) - r)) <= 6e-8 * np.max(np.abs(r)) + 1e-12
+            assert np.max(np.abs(sim.read(f) - r)) <= 1e-15 * np.max(np.abs(r))
+        # the weights the FP32 kernels read (Table 2), rounded once from FP64
+        dx, dy = 1.0 / p.nx, 1.0 / p.ny
+        a11, a12, a22 = a
+        fx = np.zeros_like(a11)
+        fx[:, :-1] = (a11[:, :-1] + a11[:, 1:]) / (2 * dx * dx)
+        fy = np.zeros_like(a22)
+        fy[:-1, :] = (a22[:-1, :] + a22[1:, :]) / (2 * dy * dy)
+        for f, r in (("face_x", fx), ("face_y", fy), ("cross", a12 / (4 * dx * dy))):
+            got = sim.read(f)
+            assert np.all(np.abs(got - r) <= 6e-8 * np.abs(r) + 1e-30), f
+        assert np.all(sim.read("face_x")[:, -1] == 0) and np.all(sim.read("face_y")[-1, :] == 0)
 
 
 @pytest.mark.parametrize("delta", [0.5, 12.5])
