@@ -75,6 +75,10 @@ def _configure(lib):
         lib.ggo_adjoint.restype = ctypes.c_int
         lib.ggo_coefficients_vjp.argtypes = [i64, _D, _D, _D, _D, _D, _D, _D, _D, _D]
         lib.ggo_coefficients_vjp.restype = None
+        lib.ggo_front_rays.argtypes = [i32, i32, dbl, dbl, _D, _D, i32, i32, dbl, dbl, dbl, _D]
+        lib.ggo_front_rays.restype = None
+        lib.ggo_front_speed.argtypes = [_D, _D, dbl, _D]
+        lib.ggo_front_speed.restype = None
     return lib
 
 
@@ -198,6 +202,31 @@ def diagnostics(U, V, W, dx, dy, eps=0.01):
     _load().ggo_diagnostics(nx, ny, dx, dy, _p(U), _p(V), _p(W), eps, _p(out))
     return dict(mass=out[0:3].copy(), min=out[3:6].copy(), max=out[6:9].copy(),
                 nonfinite=int(out[9]), tumour_area=float(out[10]), gap_area=float(out[11]))
+
+
+def front_rays(U, V, dx, dy, i0, j0, v_front=0.5, u_edge=0.5, eps=0.01):
+    """Front, healthy edge, gap width and ray integrals of V and U along the
+    east, west, north and south rays from cell (i0, j0) (Section 2's fronts
+    and interstitial gap; definitions in ggo_front_rays)."""
+    U, V = _f64(U), _f64(V)
+    ny, nx = U.shape
+    out = np.zeros(20)
+    _load().ggo_front_rays(nx, ny, dx, dy, _p(U), _p(V), int(i0), int(j0), v_front, u_edge, eps, _p(out))
+    return dict(front=out[0:4].copy(), edge=out[4:8].copy(), gap=out[8:12].copy(),
+                mass_v=out[12:16].copy(), mass_u=out[16:20].copy())
+
+
+def _front_vec(f):
+    return np.ascontiguousarray(np.concatenate([f["front"], f["edge"], f["gap"], f["mass_v"], f["mass_u"]]))
+
+
+def front_speed(before, after, elapsed):
+    """LeVeque-Yee space-averaged front speed along each ray from two
+    front_rays results taken `elapsed` time units apart."""
+    b, a = _front_vec(before), _front_vec(after)
+    out = np.zeros(4)
+    _load().ggo_front_speed(_p(b), _p(a), float(elapsed), _p(out))
+    return out
 
 
 def step_vjp(s: Setup, a11, a12, a22, U, V, W, lamU, lamV, lamW):

@@ -263,6 +263,65 @@ void ggo_diagnostics(int32_t nx, int32_t ny, double dx, double dy, const double*
     out[11] = gap * dx * dy;
 }
 
+/* ------------------------------------------------------------ front diagnostics */
+
+/* Propagating fronts and the interstitial gap of Section 2, measured along the
+ * four axis rays from the cell (i0, j0) (the centre of the initial tumour).
+ * Ray d = 0 east, 1 west, 2 north, 3 south holds the cells k = 0 .. L-1 at
+ * k cells from (i0, j0) (k = 0 is (i0, j0) itself); h = dx on the east and
+ * west rays, dy on the others; distances are from the centre of cell k = 0.
+ *   kT         the farthest cell with V > v_front (-1 if none)
+ *   kH         the first cell beyond kT with U > u_edge (L if none)
+ *   front[d]   (kT + 1/2) h, the outer face of the tumour (0 if kT = -1)
+ *   edge[d]    (kH - 1/2) h, the inner face of the healthy tissue
+ *   gap[d]     h #{k : kT < k < kH, U_k < eps and V_k < eps}
+ *   mass_v[d]  h sum_k V_k,  mass_u[d] = h sum_k U_k
+ * out[0..3] front, [4..7] edge, [8..11] gap, [12..15] mass_v, [16..19] mass_u. */
+void ggo_front_rays(int32_t nx, int32_t ny, double dx, double dy, const double* U, const double* V, int32_t i0,
+                    int32_t j0, double v_front, double u_edge, double eps, double* out)
+{
+    for (int d = 0; d < 4; ++d) {
+        int L, di = 0, dj = 0;
+        double h;
+        if (d == 0) { L = nx - i0; di = 1; h = dx; }
+        else if (d == 1) { L = i0 + 1; di = -1; h = dx; }
+        else if (d == 2) { L = ny - j0; dj = 1; h = dy; }
+        else { L = j0 + 1; dj = -1; h = dy; }
+        int kT = -1;
+        double sv = 0.0, su = 0.0;
+        for (int k = 0; k < L; ++k) {
+            double u = AT(U, i0 + di * k, j0 + dj * k), v = AT(V, i0 + di * k, j0 + dj * k);
+            if (v > v_front) kT = k;
+            sv += v;
+            su += u;
+        }
+        int kH = L;
+        for (int k = kT + 1; k < L; ++k)
+            if (AT(U, i0 + di * k, j0 + dj * k) > u_edge) { kH = k; break; }
+        int gap = 0;
+        for (int k = kT + 1; k < kH; ++k) {
+            double u = AT(U, i0 + di * k, j0 + dj * k), v = AT(V, i0 + di * k, j0 + dj * k);
+            if (u < eps && v < eps) ++gap;
+        }
+        out[d] = kT >= 0 ? (kT + 0.5) * h : 0.0;
+        out[4 + d] = (kH - 0.5) * h;
+        out[8 + d] = gap * h;
+        out[12 + d] = sv * h;
+        out[16 + d] = su * h;
+    }
+}
+
+/* Space-averaged front speed along each ray (the LeVeque-Yee formula): the
+ * rate of change of the ray integral of V divided by the jump of V across
+ * the front, from the state behind it (V = 1, both invasion regimes of
+ * Section 2) to the state ahead of it (V = 0):
+ *   speed[d] = (mass_v_after[d] - mass_v_before[d]) / (elapsed (1 - 0)).
+ * before / after are ggo_front_rays outputs. */
+void ggo_front_speed(const double* before, const double* after, double elapsed, double* speed)
+{
+    for (int d = 0; d < 4; ++d) speed[d] = (after[12 + d] - before[12 + d]) / (elapsed * (1.0 - 0.0));
+}
+
 /* ------------------------------------------------------------ discrete adjoint */
 
 /* Reverse-mode derivative of one step (ggo_step) at the state (U,V,W):

@@ -27,6 +27,12 @@ MUTATIONS = {
     "step rule without the logistic rate": ("(c + rho + 1.0 + delta)", "(c + rho + delta)"),
     "gap area with or instead of and": ("if (U[k] < eps && V[k] < eps) gap += 1.0;", "if (U[k] < eps || V[k] < eps) gap += 1.0;"),
     "Table 1 without the south face": ("return (e + w) + (n + s);", "return (e + w) + n;"),
+    "front ray: first instead of farthest tumour cell": ("if (v > v_front) kT = k;", "if (v > v_front && kT < 0) kT = k;"),
+    "front ray: healthy edge searched from the centre": ("for (int k = kT + 1; k < L; ++k)\n            if (AT(U,",
+                                                         "for (int k = 0; k < L; ++k)\n            if (AT(U,"),
+    "front ray: west ray walks east": ("else if (d == 1) { L = i0 + 1; di = -1; h = dx; }",
+                                       "else if (d == 1) { L = i0 + 1; di = 1; h = dx; }"),
+    "front speed without the elapsed time": ("/ (elapsed * (1.0 - 0.0));", "/ (1.0 - 0.0);"),
 }
 
 PIN_TESTS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_")]

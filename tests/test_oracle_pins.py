@@ -337,6 +337,106 @@ def test_diagnostics_definitions():
     assert ((U < 0.01) & (V < 0.01)).sum() == 1
 
 
+# --------------------------------------------------------------- fronts and the interstitial gap
+
+def test_front_rays_measure_a_drawn_disk_and_annulus():
+    """Tumour (V = 1) inside radius rT, healthy tissue (U = 1) outside rH,
+    nothing between: each ray sees the front at rT, the healthy edge at rH
+    and a gap of rH - rT, to within one cell of its direction; the ray
+    integral of V is the tumour radius (plus the centre cell's half)."""
+    nx, ny, lx, ly = 60, 120, 1.0, 1.0
+    dx, dy = lx / nx, ly / ny
+    i0, j0 = 30, 60
+    xc, yc = (i0 + 0.5) * dx, (j0 + 0.5) * dy
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dy
+    r = np.hypot(x[None, :] - xc, y[:, None] - yc)
+    rT, rH = 0.2, 0.3
+    V = np.where(r < rT, 1.0, 0.0)
+    U = np.where(r > rH, 1.0, 0.0)
+    f = oracle.front_rays(U, V, dx, dy, i0, j0)
+    for d, h in enumerate((dx, dx, dy, dy)):
+        assert abs(f["front"][d] - rT) <= h
+        assert abs(f["edge"][d] - rH) <= h
+        assert abs(f["gap"][d] - (rH - rT)) <= 2 * h
+        assert abs(f["mass_v"][d] - (rT + h / 2)) <= h
+    # no tumour: front 0, the healthy edge where U first exceeds 1/2
+    f0 = oracle.front_rays(U, 0 * V, dx, dy, i0, j0)
+    assert np.all(f0["front"] == 0) and np.all(f0["mass_v"] == 0)
+    assert abs(f0["edge"][0] - rH) <= dx
+    # healthy cells coexisting inside the tumour (U = 0.8 there): the edge is
+    # still the first healthy cell beyond the front
+    fc = oracle.front_rays(np.where(r < rT, 0.8, U), V, dx, dy, i0, j0)
+    for d, h in enumerate((dx, dx, dy, dy)):
+        assert abs(fc["edge"][d] - rH) <= h
+    # seen from 6 columns west of the disk centre the east front is 6 cells
+    # farther and the west front 6 cells nearer
+    fo = oracle.front_rays(U, V, dx, dy, i0 - 6, j0)
+    assert abs(fo["front"][0] - (rT + 6 * dx)) <= dx
+    assert abs(fo["front"][1] - (rT - 6 * dx)) <= dx
+
+
+def test_front_rays_are_mirror_symmetric():
+    """A state mirrored about the centre column gives equal east and west
+    results, and mirrored about the centre row equal north and south ones."""
+    nx, ny = 41, 33
+    i0, j0 = 20, 16
+    U, V, W = inputs.random_state(nx, ny, 77)
+    U = 0.5 * (U + U[:, ::-1])
+    V = 0.5 * (V + V[:, ::-1])
+    U = 0.5 * (U + U[::-1, :])
+    V = 0.5 * (V + V[::-1, :])
+    f = oracle.front_rays(U, V, 1 / nx, 1 / ny, i0, j0, v_front=0.4, u_edge=0.6, eps=0.3)
+    for key in ("front", "edge", "gap", "mass_v", "mass_u"):
+        assert f[key][0] == pytest.approx(f[key][1], rel=1e-14, abs=1e-15), key
+        assert f[key][2] == pytest.approx(f[key][3], rel=1e-14, abs=1e-15), key
+
+
+def test_front_speed_is_the_fisher_kpp_speed():
+    """With U = 0 the V equation of eq. (1) is Fisher-KPP,
+    V_t = rho V(1-V) + D V_xx, whose fronts from steep data travel at
+    2 sqrt(rho D) less a lag that decays like 3/(2 lambda t), lambda =
+    sqrt(rho/D) (Bramson).  The LeVeque-Yee speed of the scheme over
+    t in [20, 30] matches that (the lag is 3 % there) to 1.5 %, the size of
+    the next, unmodelled term of the expansion at t = 20 (a wrong D or rho
+    moves it by tens of percent), and the front position moves at the same
+    speed."""
+    nx, lx = 1000, 2.0
+    rho, D = 1.0, 2.5e-4
+    x = (np.arange(nx) + 0.5) * lx / nx
+    a = oracle.coefficients(np.zeros((1, nx)), np.full((1, nx), D), np.full((1, nx), D))
+    dt = oracle.stable_dt(nx, 1, *a, 0.0, rho, D, 0.0, lx=lx)
+    s = oracle.Setup(nx, 1, 0.0, rho, D, 0.0, dt, lx=lx)
+    U0 = np.zeros((1, nx))
+    V0 = np.where(x < 0.1, 1.0, 0.0)[None, :]
+    W0 = np.zeros((1, nx))
+    n1, n2 = int(round(20 / dt)), int(round(30 / dt))
+    U1, V1, W1 = oracle.run(s, *a, U0, V0, W0, n1)
+    U2, V2, W2 = oracle.run(s, *a, U1, V1, W1, n2 - n1)
+    assert np.all(U2 == 0)
+    f1 = oracle.front_rays(U1, V1, s.dx, s.dy, 0, 0)
+    f2 = oracle.front_rays(U2, V2, s.dx, s.dy, 0, 0)
+    elapsed = (n2 - n1) * dt
+    speed = oracle.front_speed(f1, f2, elapsed)[0]
+    cstar = 2 * np.sqrt(rho * D)
+    lam = np.sqrt(rho / D)
+    expected = cstar - 3 / (2 * lam) * np.log(30 / 20) / 10
+    assert speed == pytest.approx(expected, rel=0.015)
+    assert (f2["front"][0] - f1["front"][0]) / elapsed == pytest.approx(expected, abs=2 * s.dx / elapsed + 0.015 * cstar)
+
+
+def test_front_rays_see_the_two_invasion_regimes():
+    """Section 2: d > 1 opens an interstitial gap ahead of the tumour front,
+    d < 1 leaves none (tumour and healthy cells coexist behind the front)."""
+    for delta, has_gap in ((12.5, True), (0.5, False)):
+        x, U, V, W = _front_run(delta)
+        f = oracle.front_rays(U[None, :], V[None, :], x[1] - x[0], 1.0, 0, 0)
+        assert f["front"][0] > 0.3
+        assert (f["gap"][0] >= 0.05) == has_gap, delta
+        if not has_gap:
+            assert f["gap"][0] == 0
+
+
 # --------------------------------------------------------------- discrete adjoint
 
 def _problem_small(nx=12, ny=10, seed=101):
