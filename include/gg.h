@@ -123,6 +123,19 @@ typedef struct {
     double gap_eps;      /* threshold used (input of gg_diagnostics_eps, 0.01 by default) */
 } gg_diag;
 
+/* Fronts and the interstitial gap of Section 2 along the four axis rays from
+ * one cell (gg_front_rays).  Index d = 0 east (+x), 1 west, 2 north (+y),
+ * 3 south; ray d holds the cells k = 0 .. L-1 at k cells from the centre
+ * cell (k = 0 is the centre cell itself), h = dx on the east / west rays and
+ * dy on the others, distances measured from the centre of cell k = 0. */
+typedef struct {
+    double front[4];   /* (kT + 1/2) h, kT the farthest cell with V > v_front; 0 if none */
+    double edge[4];    /* (kH - 1/2) h, kH the first cell beyond kT with U > u_edge; L if none */
+    double gap[4];     /* h times the cells k, kT < k < kH, with U < eps and V < eps */
+    double mass_v[4];  /* h sum_k V_k along the ray */
+    double mass_u[4];  /* h sum_k U_k along the ray */
+} gg_front;
+
 typedef struct gg_sim gg_sim;
 
 /* Create a simulation of eq. (3) on one grid.
@@ -164,6 +177,28 @@ int gg_diagnostics(gg_sim* sim, gg_diag* out);
 
 /* Same as gg_diagnostics with an explicit gap threshold eps > 0. */
 int gg_diagnostics_eps(gg_sim* sim, double eps, gg_diag* out);
+
+/* Front diagnostics of the current state along the four axis rays from cell
+ * (i0, j0), 0 <= i0 < nx, 0 <= j0 < ny (normally the centre of the initial
+ * tumour): tumour front, healthy-tissue edge, interstitial-gap width and the
+ * ray integrals of V and U (gg_front above; thresholds v_front, u_edge, gap
+ * threshold eps > 0; 0.5, 0.5 and 0.01 match gg_diagnostics).  *out is a
+ * host struct.  Returns GG_OK, GG_ERR_ARG (NULL pointer, centre outside the
+ * grid, non-finite threshold, eps <= 0) or GG_ERR_CUDA.  Synchronizes. */
+int gg_front_rays(gg_sim* sim, int32_t i0, int32_t j0, double v_front, double u_edge, double eps,
+                  gg_front* out);
+
+/* Space-averaged front speed along each ray (the LeVeque-Yee formula): takes
+ * gg_front_rays into *before, advances nsteps >= 1 steps (gg_step), takes it
+ * into *after, and writes
+ *   speed[d] = (after->mass_v[d] - before->mass_v[d]) / (nsteps dt (1 - 0)),
+ * the rate of change of the ray integral of V over the jump of V across the
+ * front (V = 1 behind it in both invasion regimes of Section 2, V = 0 ahead).
+ * before, after: host structs; speed: host, 4 doubles.  Same arguments and
+ * status codes as gg_front_rays (GG_ERR_ARG also for nsteps < 1); the
+ * simulation is left nsteps steps further.  Synchronizes. */
+int gg_front_speed(gg_sim* sim, int32_t i0, int32_t j0, int64_t nsteps, double v_front, double u_edge,
+                   double eps, gg_front* before, gg_front* after, double* speed);
 
 /* Discrete adjoint of nsteps steps of eq. (3) starting from the current
  * state X^0 (the transpose of the Jacobian of each step, applied in reverse

@@ -56,6 +56,11 @@ class gg_diag(ctypes.Structure):
                 ("gap_eps", ctypes.c_double)]
 
 
+class gg_front(ctypes.Structure):
+    _fields_ = [("front", ctypes.c_double * 4), ("edge", ctypes.c_double * 4), ("gap", ctypes.c_double * 4),
+                ("mass_v", ctypes.c_double * 4), ("mass_u", ctypes.c_double * 4)]
+
+
 class GGError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{message} (status {status})")
@@ -81,6 +86,9 @@ _SIGNATURES = {
                                               ctypes.c_double, ctypes.c_double, _VP, ctypes.POINTER(gg_diag)]),
     "gg_adjoint": (ctypes.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _DP, _I64]),
     "gg_adjoint_release": (ctypes.c_int, [_VP]),
+    "gg_front_rays": (ctypes.c_int, [_VP, _I32, _I32, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP]),
+    "gg_front_speed": (ctypes.c_int, [_VP, _I32, _I32, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      _VP, _VP, _DP]),
     "gg_autotune": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(_I32)]),
     "gg_set_plan": (ctypes.c_int, [_VP, _I32, _I32, _I32, _I32]),
     "gg_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
@@ -161,6 +169,25 @@ def gg_diagnostics(sim, eps=None):
 def gg_adjoint(sim, nsteps, dLdu, dLdv, dLdw, g_theta, g_l1, g_l2, g_u0, g_v0, g_w0, g_scalars, checkpoint_every=0):
     return lib().gg_adjoint(sim, int(nsteps), dLdu, dLdv, dLdw, g_theta, g_l1, g_l2, g_u0, g_v0, g_w0,
                             g_scalars, int(checkpoint_every))
+
+
+def gg_front_rays(sim, i0, j0, v_front, u_edge, eps):
+    f = gg_front()
+    rc = lib().gg_front_rays(sim, int(i0), int(j0), float(v_front), float(u_edge), float(eps), ctypes.byref(f))
+    return rc, f
+
+
+def gg_front_speed(sim, i0, j0, nsteps, v_front, u_edge, eps):
+    b, a = gg_front(), gg_front()
+    sp = np.zeros(4)
+    rc = lib().gg_front_speed(sim, int(i0), int(j0), int(nsteps), float(v_front), float(u_edge), float(eps),
+                              ctypes.byref(b), ctypes.byref(a), sp.ctypes.data_as(_DP))
+    return rc, b, a, sp
+
+
+def front_dict(f: gg_front) -> Dict:
+    return dict(front=np.array(f.front[:]), edge=np.array(f.edge[:]), gap=np.array(f.gap[:]),
+                mass_v=np.array(f.mass_v[:]), mass_u=np.array(f.mass_u[:]))
 
 
 def gg_adjoint_release(sim):
@@ -366,6 +393,21 @@ class GGSim:
         _check(rc, self._sim, "gg_adjoint")
         res["scalars"] = gs
         return res
+
+    def front_rays(self, i0: int, j0: int, v_front: float = 0.5, u_edge: float = 0.5, eps: float = 0.01) -> Dict:
+        """Tumour front, healthy edge, gap width and ray integrals of V and U
+        along the east, west, north and south rays from cell (i0, j0)."""
+        rc, f = gg_front_rays(self._sim, i0, j0, v_front, u_edge, eps)
+        _check(rc, self._sim, "gg_front_rays")
+        return front_dict(f)
+
+    def front_speed(self, i0: int, j0: int, nsteps: int, v_front: float = 0.5, u_edge: float = 0.5,
+                    eps: float = 0.01):
+        """Advance nsteps and return (before, after, speed[4]) with the
+        LeVeque-Yee space-averaged front speed along each ray."""
+        rc, b, a, sp = gg_front_speed(self._sim, i0, j0, nsteps, v_front, u_edge, eps)
+        _check(rc, self._sim, "gg_front_speed")
+        return front_dict(b), front_dict(a), sp
 
     def release_adjoint(self):
         """Free the adjoint workspace (checkpoints, stash and kept states)."""
