@@ -210,6 +210,29 @@ def cpu_baseline_leg(p):
             "sample": f"{n} explicit steps of the {p.nx}x{p.ny} grid ({el:.1f} s)"}
 
 
+def cpu_openmp_leg(p):
+    """The same oracle source built with OpenMP over every host core (the row
+    loop of its step), a bounded sample of the same workload; a second,
+    reported CPU figure beside the one-core baseline.  None without OpenMP."""
+    import oracle
+    lib = oracle.build_openmp()
+    if lib is None:
+        return None
+    oracle.use_library(lib)
+    try:
+        s, a = oracle.setup_for(p)
+        threads = oracle.threads()
+        n = max(3, min(48, 3 * threads))
+        oracle.run(s, *a, p.u0, p.v0, p.w0, 1)  # spins up the thread pool
+        t0 = time.perf_counter()
+        oracle.run(s, *a, p.u0, p.v0, p.w0, n)
+        el = time.perf_counter() - t0
+    finally:
+        oracle.use_library(None)
+    return {"value": p.cells * n / el, "unit": "cell-updates/s", "cores": threads, "kind": "oracle (OpenMP build)",
+            "sample": f"{n} explicit steps of the {p.nx}x{p.ny} grid ({el:.1f} s)"}
+
+
 def profiled_traffic(kernel_key: str, cells: int):
     """DRAM bytes per launch of `kernel_key` from profiles/dram_traffic.txt
     (one ncu capture, scaled to `cells` by the cells processed), or None."""
@@ -391,11 +414,13 @@ def run_ours(args, dist):
 
     if dist.rank == 0:
         cpu = cpu_baseline_leg(p) if (not args.no_extras and dist.world == 1) else None
+        cpu_omp = cpu_openmp_leg(p) if (not args.no_extras and dist.world == 1) else None
         line = {
             "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(p, args, T), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "config": workload_config(p, args, T), "roofline": roofline, "cpu_baseline": cpu,
+            "cpu_baseline_omp": cpu_omp, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": ck, **extras,
         }
         print(json.dumps(line), flush=True)

@@ -34,6 +34,25 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def build_openmp() -> Optional[str]:
+    """The same source built with -fopenmp (the row loop of the step runs on
+    every host core), for the multi-core CPU baseline; None if the compiler
+    has no OpenMP."""
+    lib = os.path.join(_HERE, "liboracle_gg_omp.so")
+    if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".{os.getpid()}.tmp"
+        r = subprocess.run(["gcc", *_FLAGS, "-fopenmp", "-o", tmp, _SRC, "-lm"], capture_output=True)
+        if r.returncode != 0:
+            return None
+        os.replace(tmp, lib)
+    return lib
+
+
+def threads() -> int:
+    """Threads the loaded library's step runs on."""
+    return int(_load().ggo_threads())
+
+
 class _Problem(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
@@ -79,6 +98,8 @@ def _configure(lib):
         lib.ggo_front_rays.restype = None
         lib.ggo_front_speed.argtypes = [_D, _D, dbl, _D]
         lib.ggo_front_speed.restype = None
+        lib.ggo_threads.argtypes = []
+        lib.ggo_threads.restype = ctypes.c_int
     return lib
 
 

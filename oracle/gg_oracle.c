@@ -29,6 +29,10 @@
  *                                ghost (W_{-1,j} = W_{0,j}, corners mirrored in
  *                                both directions).
  *
+ * The row loop of ggo_step carries an OpenMP pragma; only the multi-core
+ * CPU-baseline build (-fopenmp) enables it, every other build ignores it.
+ * Each cell is computed by the same arithmetic either way.
+ *
  * Parity pins of each function are listed in tests/test_oracle_pins.py.
  * Parity unpinned: none of the functions below is unpinned, but the paper
  * prints no numerical result, so agreement with the authors' own code cannot
@@ -38,6 +42,19 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads the step runs on: omp_get_max_threads() in the OpenMP build, else 1. */
+int ggo_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 typedef struct {
     int32_t nx, ny;      /* cells in x and y */
@@ -187,6 +204,7 @@ void ggo_step(const ggo_problem* p, const double* a11, const double* a12, const 
 {
     int nx = p->nx, ny = p->ny;
     double dt = p->dt;
+#pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             double u = AT(U, i, j), v = AT(V, i, j), w = AT(W, i, j);

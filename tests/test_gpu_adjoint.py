@@ -52,7 +52,7 @@ def gpu_adjoint(torch, p, steps, dLdU, dLdV, dLdW, precision="fp32_kahan", check
     return r
 
 
-@pytest.mark.parametrize("nx,ny,steps", [(40, 33, 120), (64, 64, 200), (5, 1, 50), (1, 6, 50)])
+@pytest.mark.parametrize("nx,ny,steps", [(40, 33, 120), (64, 64, 200), (256, 256, 100), (5, 1, 50), (1, 6, 50)])
 def test_adjoint_matches_oracle(torch, nx, ny, steps):
     p = small_problem(nx, ny, steps=steps)
     Vstar = inputs.random_state(nx, ny, 99)[1]

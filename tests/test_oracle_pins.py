@@ -540,3 +540,4 @@ def test_coefficient_chain_rule_matches_finite_differences():
         Ap, Am = oracle.coefficients(*p), oracle.coefficients(*m)
         fd = sum((x - y) / (2 * eps) * gg for x, y, gg in zip(Ap, Am, g))
         assert np.max(np.abs(fd - grad)) < 1e-9
+
