@@ -55,6 +55,8 @@ Rates32 make_rates32(double dx, double dy, double dt, const gg_params& p)
     r.Ky = (float)(p.D / (dy * dy));
     r.hKx = (float)(0.5 * p.D / (dx * dx));
     r.hKy = (float)(0.5 * p.D / (dy * dy));
+    r.K2 = make_float2(r.Kx, r.Ky);
+    r.nhK2 = make_float2(-r.hKx, -r.hKy);
     r.no_reaction = (p.flags & GG_FLAG_NO_REACTION) ? 1 : 0;
     return r;
 }

@@ -40,6 +40,7 @@ struct Rates32 {
     float ihx2, ihy2;     // 1/dx^2, 1/dy^2
     float Kx, Ky;         // D/dx^2, D/dy^2 (tumour face weights, D folded in)
     float hKx, hKy;       // Kx/2, Ky/2
+    float2 K2, nhK2;      // (Kx, Ky) and (-hKx, -hKy), for packed east / north faces
     int no_reaction;
 };
 Rates32 make_rates32(double dx, double dy, double dt, const gg_params& p);

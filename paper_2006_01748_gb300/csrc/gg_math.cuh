@@ -74,5 +74,10 @@ __device__ __forceinline__ void kahan_step(float x, float dt, float f, float com
 
 __device__ __forceinline__ float euler_step(float x, float dt, float f) { return __fmaf_rn(dt, f, x); }
 
+// Packed pairs (sm_100 family): each lane is the same IEEE round-to-nearest
+// operation as the scalar intrinsic, so packed and scalar code give the same
+// bits.  a - b is formed as fma(b, -1, a), one rounding of a - b.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
 }  // namespace fvm
 }  // namespace gg

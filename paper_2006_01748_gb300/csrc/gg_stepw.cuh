@@ -62,21 +62,24 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
     const int hiT = min(ny, ys + H);
     const int nticks = hiT - lo0 + T;
 
-    // windows of level t-1 used by level t, index t-1
-    float sW[T], pU[T], pV[T], pW[T], nU[T], nV[T], nW[T];
-    float cP[T][3], cN[T][3];
-    float cf[T + 1][3];  // [age][ax, b, ay]; age a holds input row R - a
+    // windows of level t-1 used by level t, index t-1; u and v (and their
+    // Kahan terms) as pairs for the packed arithmetic
+    float2 pUV[T], nUV[T], cPuv[T], cNuv[T];
+    float sW[T], pW[T], nW[T], cPw[T], cNw[T];
+    float2 cfA[T + 1];   // [age] (ax, ay); age a holds input row R - a
+    float cfB[T + 1];    // [age] b
     float carG[T + 1], carH[T + 1];           // north faces of the previous tick
     float carWE[T + 1], carZ[T + 1];          // east w and y cross term of the own row
+    const float2 dt2 = make_float2(k.dt, k.dt);
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-        sW[t] = pU[t] = pV[t] = pW[t] = nU[t] = nV[t] = nW[t] = 0.0f;
-#pragma unroll
-        for (int f = 0; f < 3; ++f) cP[t][f] = cN[t][f] = 0.0f;
+        pUV[t] = nUV[t] = cPuv[t] = cNuv[t] = make_float2(0.0f, 0.0f);
+        sW[t] = pW[t] = nW[t] = cPw[t] = cNw[t] = 0.0f;
     }
 #pragma unroll
     for (int a = 0; a <= T; ++a) {
-        cf[a][0] = cf[a][1] = cf[a][2] = 0.0f;
+        cfA[a] = make_float2(0.0f, 0.0f);
+        cfB[a] = 0.0f;
         carG[a] = carH[a] = carWE[a] = carZ[a] = 0.0f;
     }
 
@@ -105,19 +108,16 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
         // input row R enters the tensor window and level 0
 #pragma unroll
         for (int a = T; a > 0; --a) {
-            cf[a][0] = cf[a - 1][0];
-            cf[a][1] = cf[a - 1][1];
-            cf[a][2] = cf[a - 1][2];
+            cfA[a] = cfA[a - 1];
+            cfB[a] = cfB[a - 1];
         }
-        cf[0][0] = in[3]; cf[0][1] = in[4]; cf[0][2] = in[5];
-        sW[0] = pW[0]; pU[0] = nU[0]; pV[0] = nV[0]; pW[0] = nW[0];
-        nU[0] = in[0]; nV[0] = in[1]; nW[0] = in[2];
+        cfA[0] = make_float2(in[3], in[5]);
+        cfB[0] = in[4];
+        sW[0] = pW[0]; pUV[0] = nUV[0]; pW[0] = nW[0];
+        nUV[0] = make_float2(in[0], in[1]); nW[0] = in[2];
         if constexpr (KAHAN) {
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                cP[0][f] = cN[0][f];
-                cN[0][f] = in[6 + f];
-            }
+            cPuv[0] = cNuv[0]; cPw[0] = cNw[0];
+            cNuv[0] = make_float2(in[6], in[7]); cNw[0] = in[8];
         }
         if (R + 2 < hi0) fetch(R + 2, in);  // two rows ahead
 
@@ -126,17 +126,18 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
             const int q = R - t;
             const bool valid = q >= max(0, ys - T + t) && q < min(ny, ys + H + T - t);  // warp-uniform
             const bool hasS = YEDGE ? q > 0 : true, hasN = YEDGE ? q + 1 < ny : true;
-            const float uP = pU[t - 1], vP = pV[t - 1], wP = pW[t - 1];
-            const float uN = nU[t - 1], vN = nV[t - 1], wN = nW[t - 1];
-            const float axP = cf[t][0], bP = cf[t][1], ayP = cf[t][2];
-            const float bN = cf[t - 1][1];
+            const float2 uvP = pUV[t - 1], uvN = nUV[t - 1];
+            const float wP = pW[t - 1], wN = nW[t - 1];
+            const float2 axy = cfA[t];
+            const float bP = cfB[t], bN = cfB[t - 1];
             // x cross term of the own row (tangential difference mirrored at
             // the south / north boundary), shared with the west neighbour
             const float zxP = fvm::cross(bP, __fsub_rn(hasN ? wN : wP, hasS ? sW[t - 1] : wP));
-            float uE = from_east(uP), vE = from_east(vP), zxE = from_east(zxP);
+            float2 uvE = make_float2(from_east(uvP.x), from_east(uvP.y));
+            float zxE = from_east(zxP);
             float wNE = from_east(wN), wNW = from_west(wN);
             if constexpr (EDGE) {
-                if (!hasE) { uE = uP; vE = vP; wNE = wN; }
+                if (!hasE) { uvE = uvP; wNE = wN; }
                 if (!hasW) wNW = wN;
             }
             // east w of the own row: the north row's of the last tick
@@ -145,41 +146,64 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
             // y cross terms of the own row (last tick's north row) and the north row
             const float zyP = carZ[t], zyN = fvm::cross(bN, __fsub_rn(wNE, wNW));
             carZ[t] = zyN;
-            float gE = fvm::g_face(axP, wP, wE, zxP, zxE);
-            float hE = fvm::h_face(uP, uE, vP, vE, k.Kx, k.hKx);
+            // east and north faces as (x, y) pairs: the acid flux
+            // a (W_R - W_L) + (z_L + z_R) and the tumour flux
+            // (K - K/2 (U_L + U_R)) (V_R - V_L) of gg_math.cuh
+            const float2 dw = make_float2(__fsub_rn(wE, wP), __fsub_rn(wN, wP));
+            const float2 zs = make_float2(__fadd_rn(zxP, zxE), __fadd_rn(zyP, zyN));
+            float2 gf = __ffma2_rn(axy, dw, zs);
+            const float2 su = make_float2(__fadd_rn(uvP.x, uvE.x), __fadd_rn(uvP.x, uvN.x));
+            const float2 dv = make_float2(__fsub_rn(uvE.y, uvP.y), __fsub_rn(uvN.y, uvP.y));
+            float2 hf = __fmul2_rn(__ffma2_rn(k.nhK2, su, k.K2), dv);
             if constexpr (EDGE) {
-                if (!hasE) { gE = 0.0f; hE = 0.0f; }
+                if (!hasE) { gf.x = 0.0f; hf.x = 0.0f; }
             }
-            const float gN = hasN ? fvm::g_face(ayP, wP, wN, zyP, zyN) : 0.0f;
-            const float hN = hasN ? fvm::h_face(uP, uN, vP, vN, k.Ky, k.hKy) : 0.0f;
-            float gW = from_west(gE), hW = from_west(hE);
+            if (!hasN) { gf.y = 0.0f; hf.y = 0.0f; }
+            float gW = from_west(gf.x), hW = from_west(hf.x);
             if constexpr (EDGE) {
                 if (!hasW) { gW = 0.0f; hW = 0.0f; }
             }
             const float gS = hasS ? carG[t] : 0.0f, hS = hasS ? carH[t] : 0.0f;
-            carG[t] = gN;
-            carH[t] = hN;
+            carG[t] = gf.y;
+            carH[t] = hf.y;
+            // D D1 = (hE - hW) + (hN - hS), D2 = (gE - gW) + (gN - gS)
+            const float2 eh = fvm::sub2(hf, make_float2(hW, hS));
+            const float2 eg = fvm::sub2(gf, make_float2(gW, gS));
+            const float d1 = __fadd_rn(eh.x, eh.y), d2 = __fadd_rn(eg.x, eg.y);
             float fu, fv, fw;
-            fvm::rates_faces(k, uP, vP, wP, hE, hW, hN, hS, gE, gW, gN, gS, fu, fv, fw);
-            float un, vn, wn, cun = 0.0f, cvn = 0.0f, cwn = 0.0f;
-            if constexpr (KAHAN) {
-                fvm::kahan_step(uP, k.dt, fu, cP[t - 1][0], un, cun);
-                fvm::kahan_step(vP, k.dt, fv, cP[t - 1][1], vn, cvn);
-                fvm::kahan_step(wP, k.dt, fw, cP[t - 1][2], wn, cwn);
+            if (k.no_reaction) {
+                fu = 0.0f;
+                fv = d1;
+                fw = d2;
             } else {
-                un = fvm::euler_step(uP, k.dt, fu);
-                vn = fvm::euler_step(vP, k.dt, fv);
+                // U((1-U) - delta W),  rho V (1-V) + D D1,  c (V-W) + D2
+                const float2 om = fvm::sub2(make_float2(1.0f, 1.0f), uvP);
+                fu = __fmul_rn(uvP.x, __fmaf_rn(-k.delta, wP, om.x));
+                fv = __fmaf_rn(__fmul_rn(k.rho, uvP.y), om.y, d1);
+                fw = __fmaf_rn(k.c, __fsub_rn(uvP.y, wP), d2);
+            }
+            float2 uvn, cuvn = make_float2(0.0f, 0.0f);
+            float wn, cwn = 0.0f;
+            if constexpr (KAHAN) {
+                // kahan_step of gg_math.cuh on the (u, v) pair and on w
+                const float2 c0 = cPuv[t - 1];
+                const float2 y = __ffma2_rn(dt2, make_float2(fu, fv), make_float2(-c0.x, -c0.y));
+                uvn = __fadd2_rn(uvP, y);
+                cuvn = fvm::sub2(fvm::sub2(uvn, uvP), y);
+                fvm::kahan_step(wP, k.dt, fw, cPw[t - 1], wn, cwn);
+            } else {
+                uvn = __ffma2_rn(dt2, make_float2(fu, fv), uvP);
                 wn = fvm::euler_step(wP, k.dt, fw);
             }
             if (t == T) {
                 if (valid && outc) {
                     const size_t o = (size_t)q * pitch + gx;
-                    g.uo[o] = un;
-                    g.vo[o] = vn;
+                    g.uo[o] = uvn.x;
+                    g.vo[o] = uvn.y;
                     g.wo[o] = wn;
                     if constexpr (KAHAN) {
-                        g.cuo[o] = cun;
-                        g.cvo[o] = cvn;
+                        g.cuo[o] = cuvn.x;
+                        g.cvo[o] = cuvn.y;
                         g.cwo[o] = cwn;
                     }
                 }
@@ -189,17 +213,17 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
                     if (q >= ys && q < hiT && outc) {
                         const size_t o = (size_t)q * pitch + gx;
                         const int li = (t < T) ? t - 1 : 0;
-                        stash->u[li][o] = un;
-                        stash->v[li][o] = vn;
+                        stash->u[li][o] = uvn.x;
+                        stash->v[li][o] = uvn.y;
                         stash->w[li][o] = wn;
                     }
                 }
                 const int tt = (t < T) ? t : 0;  // level t passes row q on
-                sW[tt] = pW[tt]; pU[tt] = nU[tt]; pV[tt] = nV[tt]; pW[tt] = nW[tt];
-                nU[tt] = un; nV[tt] = vn; nW[tt] = wn;
+                sW[tt] = pW[tt]; pUV[tt] = nUV[tt]; pW[tt] = nW[tt];
+                nUV[tt] = uvn; nW[tt] = wn;
                 if constexpr (KAHAN) {
-                    cP[tt][0] = cN[tt][0]; cP[tt][1] = cN[tt][1]; cP[tt][2] = cN[tt][2];
-                    cN[tt][0] = cun; cN[tt][1] = cvn; cN[tt][2] = cwn;
+                    cPuv[tt] = cNuv[tt]; cPw[tt] = cNw[tt];
+                    cNuv[tt] = cuvn; cNw[tt] = cwn;
                 }
             }
         }
