@@ -310,14 +310,20 @@ def run_ours(args, dist):
     value = p.cells * n_inner * args.steps * dist.world / (ms_max / 1e3)
 
     peak, peak_kind = measured_peaks()
-    kname = f"stepw_kernel<T={T},Kahan>" if plan["kind"] == "warp" else f"step32_kernel<T={T},Kahan>"
+    if plan["kind"] == "warp":
+        kname = "stepw1_kernel<Kahan>" if T == 1 else f"stepw_kernel<T={T},Kahan>"
+    else:
+        kname = f"step32_kernel<T={T},Kahan>"
     alg_bytes = BYTES_PER_CELL_PASS["fp32_kahan"] * p.cells
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
     traffic = profiled_traffic(f"{plan['kind']} T={T} kahan chunk={plan['by']}", p.cells)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": kname, "chunk_rows": plan["by"],
                 "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": launch_ms,
-                "note": "one launch = one pass of T explicit steps: 60 B/cell of state and tensor traffic"}
+                "note": "one launch = one pass of T explicit steps: 60 B/cell of state and tensor traffic",
+                # temporally blocked: the same throughput against the roof of the one-step pass
+                # (60 B per cell-update at the measured HBM bandwidth)
+                "t1_roof_cell_updates_per_s": peak * 1e9 / 60, "value_over_t1_roof": value / dist.world / (peak * 1e9 / 60)}
 
     extras = {}
     if not args.no_extras:
@@ -333,7 +339,7 @@ def run_ours(args, dist):
             ach2 = bpc * p.cells / (ms2 / 1e3 / n2) / 1e9
             extras[name] = {"value": p.cells * n2 / (ms2 / 1e3), "unit": "cell-updates/s",
                             "roofline": {"bound": "hbm", "achieved": ach2, "peak": peak, "unit": "GB/s",
-                                         "frac": ach2 / peak, "kernel": f"stepw_kernel<T=1,{prec}>",
+                                         "frac": ach2 / peak, "kernel": f"stepw1_kernel<{prec}>",
                                          "chunk_rows": pl2["by"],
                                          "traffic": profiled_traffic(f"warp T=1 {'kahan' if prec == 'fp32_kahan' else 'plain'}"
                                                                      f" chunk={pl2['by']}", p.cells)}}

@@ -256,7 +256,7 @@ int gg_diagnostics_noalloc(const void* u, const void* v, const void* w, int32_t 
                            int32_t nx, int32_t ny, int32_t pitch, double dx, double dy,
                            double eps, void* cuda_stream, gg_diag* out);
 
-/* Autotuner of the FP32 step: times trial_steps steps (0 means 24) of every
+/* Autotuner of the FP32 step: times trial_steps steps (0 means 48) of every
  * candidate launch plan -- the warp-register wavefront with T = 1..4 steps
  * per pass and chunk heights 16..256 rows, the shared-memory wavefront with
  * T in {1, 2, 4, 8} -- on this simulation, keeps the fastest and restores the

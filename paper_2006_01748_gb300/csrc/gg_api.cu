@@ -141,21 +141,27 @@ Plan32 tune_plan(gg_sim* s, int64_t trial_steps)
 {
     const bool kahan = s->params.precision == GG_FP32_KAHAN;
     const int nstate = kahan ? 6 : 3;
-    if (trial_steps < 1) trial_steps = 24;
+    if (trial_steps < 1) trial_steps = 48;
     const int64_t n = (trial_steps + 23) / 24 * 24;  // a multiple of every T tried
     std::vector<Plan32> cands;
     for (int T = 1; T <= 4; ++T) {
-        // fixed heights, and the heights for which the grid fills 1..4 whole
-        // waves of resident warps (a partial last wave costs nearly a full one)
+        // fixed heights, and the four largest heights (at most 256 rows) for
+        // which the grid fills a whole number of waves of resident warps (a
+        // partial last wave costs nearly a full one)
         std::vector<int> Hs = {16, 32, 64, 128, 256};
         const int wave = stepw_wave_warps(T, kahan);
         const int strips = (s->nx + 32 - 2 * T - 1) / (32 - 2 * T);
-        if (wave > 0 && strips <= wave)
-            for (int m = 1; m <= 4; ++m) {
+        if (wave > 0 && strips <= wave) {
+            int added = 0;
+            for (int m = 1; added < 4; ++m) {
                 const int nch = m * (wave / strips);
                 const int H = (s->ny + nch - 1) / nch;
-                if (H <= 256 && std::find(Hs.begin(), Hs.end(), H) == Hs.end()) Hs.push_back(H);
+                if (H < 4 * T + 8) break;
+                if (H > 256) continue;
+                if (std::find(Hs.begin(), Hs.end(), H) == Hs.end()) Hs.push_back(H);
+                ++added;
             }
+        }
         for (int H : Hs) {
             if (H < 4 * T + 8 && H != 256) continue;
             Plan32 p = default_plan(s->nx, s->ny, T);

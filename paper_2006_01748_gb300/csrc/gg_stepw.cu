@@ -1,12 +1,13 @@
 // Launchers of the warp-register wavefront step (kernel body in gg_stepw.cuh).
 //
-// CTA size: for T >= 2 one warp per CTA.  The warps share nothing, and with
-// a 32-thread bound the compiler keeps the T = 3 Kahan kernel at 120
-// registers (T = 4 at 152) without spills, so that 17 (13) warps fit on an
-// SM; with 4-warp CTAs it allocated 135 (168, with spills) and the SM held
-// 12.  Measured on the 8192^2 tissue: T = 3 225 vs 183 G cell-steps/s.  The
-// T = 1 kernel (64 registers, short-lived warps) keeps 4-warp CTAs, which
-// measured 105 vs 96 G cell-steps/s.
+// CTA size: for T >= 2 one warp per CTA (stepw_kernel).  The warps share
+// nothing, and under a 32-thread bound the compiler keeps the Kahan kernels
+// at 123 (T = 3) and 137 (T = 4) registers without spills, so that 16 (14)
+// warps fit on an SM; with 4-warp CTAs the (scalar) T = 3 kernel took 135
+// registers and the SM held 12 warps: 183 against 225 G cell-steps/s on the
+// 8192^2 tissue.  The one-step pass (stepw1_kernel, HBM-bound, short-lived
+// warps) keeps 4-warp CTAs bound to 6 or 8 per SM: 105 against 96 G
+// cell-steps/s with one warp per CTA.
 #include "gg_stepw.cuh"
 
 namespace gg {
@@ -15,14 +16,27 @@ namespace {
 template <int T> constexpr int warps_per_cta() { return T == 1 ? 4 : 1; }
 
 template <int T, bool KAHAN>
-__global__ void __launch_bounds__(32 * warps_per_cta<T>()) stepw_kernel(const Grid32 g, const Rates32 k, const int H,
-                                                                        const int nstrips, const int nwarps)
+__global__ void __launch_bounds__(32) stepw_kernel(const Grid32 g, const Rates32 k, const int H, const int nstrips,
+                                                   const int nwarps)
 {
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * warps_per_cta<T>() + (threadIdx.x >> 5);
-    if (gw >= nwarps) return;  // whole warps only
+    const int lane = threadIdx.x;
+    const int gw = blockIdx.x;
+    if (gw >= nwarps) return;
     const int strip = gw % nstrips, chunk = gw / nstrips;
     stepw::warp_pass_any<T, KAHAN>(g, k, H, strip, chunk, lane);
+}
+
+// The one-step pass needs occupancy to hide HBM latency: 4-warp CTAs, bound
+// to 8 per SM without Kahan terms (64 registers) and 6 with them (80).
+template <bool KAHAN>
+__global__ void __launch_bounds__(128, KAHAN ? 6 : 8) stepw1_kernel(const Grid32 g, const Rates32 k, const int H,
+                                                                     const int nstrips, const int nwarps)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (gw >= nwarps) return;  // whole warps only
+    const int strip = gw % nstrips, chunk = gw / nstrips;
+    stepw::warp_pass_any<1, KAHAN>(g, k, H, strip, chunk, lane);
 }
 
 template <int T, bool KAHAN>
@@ -54,8 +68,8 @@ cudaError_t launch_w(const Grid32& g, const Rates32& r, int H, cudaStream_t s)
     const int nstrips = (g.nx + OUT - 1) / OUT;
     const int nchunks = (g.ny + H - 1) / H;
     const int nwarps = nstrips * nchunks;
-    constexpr int wpc = warps_per_cta<T>();
-    stepw_kernel<T, KAHAN><<<(nwarps + wpc - 1) / wpc, 32 * wpc, 0, s>>>(g, r, H, nstrips, nwarps);
+    if constexpr (T == 1) stepw1_kernel<KAHAN><<<(nwarps + 3) / 4, 128, 0, s>>>(g, r, H, nstrips, nwarps);
+    else stepw_kernel<T, KAHAN><<<nwarps, 32, 0, s>>>(g, r, H, nstrips, nwarps);
     return cudaGetLastError();
 }
 
@@ -64,9 +78,13 @@ int wave_warps_T()
 {
     constexpr int wpc = warps_per_cta<T>();
     int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stepw_kernel<T, KAHAN>, 32 * wpc, 0) != cudaSuccess) {
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) {
+        if constexpr (T == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stepw1_kernel<KAHAN>, 128, 0);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stepw_kernel<T, KAHAN>, 32, 0);
+    }
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }

@@ -21,12 +21,22 @@
 // warp writes its 32 - 2T middle columns and neighbouring strips overlap by
 // 2T columns.  Warps that touch the west or east domain boundary run a
 // variant with the boundary conditions; interior warps skip them.
+#include <type_traits>
+
 #include "gg_math.cuh"
 
 namespace gg {
 namespace stepw {
 
 constexpr unsigned kFull = 0xffffffffu;
+
+// Two floats without the pair alignment of float2: the one-step pass keeps
+// its (u, v) windows in this form, so that the compiler allocates them as
+// independent scalars.
+struct F2 {
+    float x, y;
+};
+template <typename V> __device__ __forceinline__ V mk2(float a, float b) { return V{a, b}; }
 
 __device__ __forceinline__ float from_west(float x) { return __shfl_up_sync(kFull, x, 1); }
 __device__ __forceinline__ float from_east(float x) { return __shfl_down_sync(kFull, x, 1); }
@@ -50,6 +60,9 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
                                           const int chunk, const int lane, const Stash32* stash = nullptr)
 {
     constexpr int OUT = 32 - 2 * T;
+    // packed FP32 pairs for T >= 2 (issue-bound); the one-step pass is
+    // HBM-bound and keeps scalar code, which needs fewer registers
+    constexpr bool PK = T >= 2;
     const int nx = g.nx, ny = g.ny, pitch = g.pitch;
     const int gx = strip * OUT - T + lane;
     const bool ind = EDGE ? (gx >= 0 && gx < nx) : true;
@@ -64,21 +77,22 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
 
     // windows of level t-1 used by level t, index t-1; u and v (and their
     // Kahan terms) as pairs for the packed arithmetic
-    float2 pUV[T], nUV[T], cPuv[T], cNuv[T];
+    using V2 = typename std::conditional<PK, float2, F2>::type;
+    V2 pUV[T], nUV[T], cPuv[T], cNuv[T];
     float sW[T], pW[T], nW[T], cPw[T], cNw[T];
-    float2 cfA[T + 1];   // [age] (ax, ay); age a holds input row R - a
+    V2 cfA[T + 1];       // [age] (ax, ay); age a holds input row R - a
     float cfB[T + 1];    // [age] b
     float carG[T + 1], carH[T + 1];           // north faces of the previous tick
     float carWE[T + 1], carZ[T + 1];          // east w and y cross term of the own row
-    const float2 dt2 = make_float2(k.dt, k.dt);
+    const float2 dt2 = make_float2(k.dt, k.dt);  // used by the packed body only
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-        pUV[t] = nUV[t] = cPuv[t] = cNuv[t] = make_float2(0.0f, 0.0f);
+        pUV[t] = nUV[t] = cPuv[t] = cNuv[t] = mk2<V2>(0.0f, 0.0f);
         sW[t] = pW[t] = nW[t] = cPw[t] = cNw[t] = 0.0f;
     }
 #pragma unroll
     for (int a = 0; a <= T; ++a) {
-        cfA[a] = make_float2(0.0f, 0.0f);
+        cfA[a] = mk2<V2>(0.0f, 0.0f);
         cfB[a] = 0.0f;
         carG[a] = carH[a] = carWE[a] = carZ[a] = 0.0f;
     }
@@ -111,13 +125,13 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
             cfA[a] = cfA[a - 1];
             cfB[a] = cfB[a - 1];
         }
-        cfA[0] = make_float2(in[3], in[5]);
+        cfA[0] = mk2<V2>(in[3], in[5]);
         cfB[0] = in[4];
         sW[0] = pW[0]; pUV[0] = nUV[0]; pW[0] = nW[0];
-        nUV[0] = make_float2(in[0], in[1]); nW[0] = in[2];
+        nUV[0] = mk2<V2>(in[0], in[1]); nW[0] = in[2];
         if constexpr (KAHAN) {
             cPuv[0] = cNuv[0]; cPw[0] = cNw[0];
-            cNuv[0] = make_float2(in[6], in[7]); cNw[0] = in[8];
+            cNuv[0] = mk2<V2>(in[6], in[7]); cNw[0] = in[8];
         }
         if (R + 2 < hi0) fetch(R + 2, in);  // two rows ahead
 
@@ -126,14 +140,14 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
             const int q = R - t;
             const bool valid = q >= max(0, ys - T + t) && q < min(ny, ys + H + T - t);  // warp-uniform
             const bool hasS = YEDGE ? q > 0 : true, hasN = YEDGE ? q + 1 < ny : true;
-            const float2 uvP = pUV[t - 1], uvN = nUV[t - 1];
+            const V2 uvP = pUV[t - 1], uvN = nUV[t - 1];
             const float wP = pW[t - 1], wN = nW[t - 1];
-            const float2 axy = cfA[t];
+            const V2 axy = cfA[t];
             const float bP = cfB[t], bN = cfB[t - 1];
             // x cross term of the own row (tangential difference mirrored at
             // the south / north boundary), shared with the west neighbour
             const float zxP = fvm::cross(bP, __fsub_rn(hasN ? wN : wP, hasS ? sW[t - 1] : wP));
-            float2 uvE = make_float2(from_east(uvP.x), from_east(uvP.y));
+            V2 uvE = mk2<V2>(from_east(uvP.x), from_east(uvP.y));
             float zxE = from_east(zxP);
             float wNE = from_east(wN), wNW = from_west(wN);
             if constexpr (EDGE) {
@@ -149,12 +163,19 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
             // east and north faces as (x, y) pairs: the acid flux
             // a (W_R - W_L) + (z_L + z_R) and the tumour flux
             // (K - K/2 (U_L + U_R)) (V_R - V_L) of gg_math.cuh
-            const float2 dw = make_float2(__fsub_rn(wE, wP), __fsub_rn(wN, wP));
-            const float2 zs = make_float2(__fadd_rn(zxP, zxE), __fadd_rn(zyP, zyN));
-            float2 gf = __ffma2_rn(axy, dw, zs);
-            const float2 su = make_float2(__fadd_rn(uvP.x, uvE.x), __fadd_rn(uvP.x, uvN.x));
-            const float2 dv = make_float2(__fsub_rn(uvE.y, uvP.y), __fsub_rn(uvN.y, uvP.y));
-            float2 hf = __fmul2_rn(__ffma2_rn(k.nhK2, su, k.K2), dv);
+            V2 gf, hf;
+            if constexpr (PK) {
+                const float2 dw = make_float2(__fsub_rn(wE, wP), __fsub_rn(wN, wP));
+                const float2 zs = make_float2(__fadd_rn(zxP, zxE), __fadd_rn(zyP, zyN));
+                gf = __ffma2_rn(axy, dw, zs);
+                const float2 su = make_float2(__fadd_rn(uvP.x, uvE.x), __fadd_rn(uvP.x, uvN.x));
+                const float2 dv = make_float2(__fsub_rn(uvE.y, uvP.y), __fsub_rn(uvN.y, uvP.y));
+                hf = __fmul2_rn(__ffma2_rn(k.nhK2, su, k.K2), dv);
+            } else {
+                gf = mk2<V2>(fvm::g_face(axy.x, wP, wE, zxP, zxE), fvm::g_face(axy.y, wP, wN, zyP, zyN));
+                hf = mk2<V2>(fvm::h_face(uvP.x, uvE.x, uvP.y, uvE.y, k.Kx, k.hKx),
+                             fvm::h_face(uvP.x, uvN.x, uvP.y, uvN.y, k.Ky, k.hKy));
+            }
             if constexpr (EDGE) {
                 if (!hasE) { gf.x = 0.0f; hf.x = 0.0f; }
             }
@@ -166,33 +187,44 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
             const float gS = hasS ? carG[t] : 0.0f, hS = hasS ? carH[t] : 0.0f;
             carG[t] = gf.y;
             carH[t] = hf.y;
-            // D D1 = (hE - hW) + (hN - hS), D2 = (gE - gW) + (gN - gS)
-            const float2 eh = fvm::sub2(hf, make_float2(hW, hS));
-            const float2 eg = fvm::sub2(gf, make_float2(gW, gS));
-            const float d1 = __fadd_rn(eh.x, eh.y), d2 = __fadd_rn(eg.x, eg.y);
             float fu, fv, fw;
-            if (k.no_reaction) {
-                fu = 0.0f;
-                fv = d1;
-                fw = d2;
+            if constexpr (PK) {
+                // D D1 = (hE - hW) + (hN - hS), D2 = (gE - gW) + (gN - gS)
+                const float2 eh = fvm::sub2(hf, make_float2(hW, hS));
+                const float2 eg = fvm::sub2(gf, make_float2(gW, gS));
+                const float d1 = __fadd_rn(eh.x, eh.y), d2 = __fadd_rn(eg.x, eg.y);
+                if (k.no_reaction) {
+                    fu = 0.0f;
+                    fv = d1;
+                    fw = d2;
+                } else {
+                    // U((1-U) - delta W),  rho V (1-V) + D D1,  c (V-W) + D2
+                    const float2 om = fvm::sub2(make_float2(1.0f, 1.0f), uvP);
+                    fu = __fmul_rn(uvP.x, __fmaf_rn(-k.delta, wP, om.x));
+                    fv = __fmaf_rn(__fmul_rn(k.rho, uvP.y), om.y, d1);
+                    fw = __fmaf_rn(k.c, __fsub_rn(uvP.y, wP), d2);
+                }
             } else {
-                // U((1-U) - delta W),  rho V (1-V) + D D1,  c (V-W) + D2
-                const float2 om = fvm::sub2(make_float2(1.0f, 1.0f), uvP);
-                fu = __fmul_rn(uvP.x, __fmaf_rn(-k.delta, wP, om.x));
-                fv = __fmaf_rn(__fmul_rn(k.rho, uvP.y), om.y, d1);
-                fw = __fmaf_rn(k.c, __fsub_rn(uvP.y, wP), d2);
+                fvm::rates_faces(k, uvP.x, uvP.y, wP, hf.x, hW, hf.y, hS, gf.x, gW, gf.y, gS, fu, fv, fw);
             }
-            float2 uvn, cuvn = make_float2(0.0f, 0.0f);
+            V2 uvn, cuvn = mk2<V2>(0.0f, 0.0f);
             float wn, cwn = 0.0f;
-            if constexpr (KAHAN) {
+            if constexpr (KAHAN && PK) {
                 // kahan_step of gg_math.cuh on the (u, v) pair and on w
                 const float2 c0 = cPuv[t - 1];
                 const float2 y = __ffma2_rn(dt2, make_float2(fu, fv), make_float2(-c0.x, -c0.y));
                 uvn = __fadd2_rn(uvP, y);
                 cuvn = fvm::sub2(fvm::sub2(uvn, uvP), y);
                 fvm::kahan_step(wP, k.dt, fw, cPw[t - 1], wn, cwn);
-            } else {
+            } else if constexpr (KAHAN) {
+                fvm::kahan_step(uvP.x, k.dt, fu, cPuv[t - 1].x, uvn.x, cuvn.x);
+                fvm::kahan_step(uvP.y, k.dt, fv, cPuv[t - 1].y, uvn.y, cuvn.y);
+                fvm::kahan_step(wP, k.dt, fw, cPw[t - 1], wn, cwn);
+            } else if constexpr (PK) {
                 uvn = __ffma2_rn(dt2, make_float2(fu, fv), uvP);
+                wn = fvm::euler_step(wP, k.dt, fw);
+            } else {
+                uvn = mk2<V2>(fvm::euler_step(uvP.x, k.dt, fu), fvm::euler_step(uvP.y, k.dt, fv));
                 wn = fvm::euler_step(wP, k.dt, fw);
             }
             if (t == T) {
