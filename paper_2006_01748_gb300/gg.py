@@ -328,12 +328,16 @@ class GGSim:
         return dict(T=chosen[0], kind="warp" if chosen[1] == 1 else "smem", bx=chosen[2], by=chosen[3])
 
     def read(self, field: str = "v", fp64: bool = True, out=None):
-        """Copy a field; into a new host numpy array, or into ``out`` (a
-        contiguous torch CUDA tensor of nx*ny float32/float64 values)."""
+        """Copy a field; into a new host numpy array, into ``out`` when it is
+        a C-contiguous host numpy array of nx*ny float32/float64 values (for
+        instance one backed by pinned memory), or into ``out`` when it is a
+        contiguous torch CUDA tensor of nx*ny float32/float64 values."""
         f = FIELDS[field]
-        if out is None:
-            a = np.empty((self.ny, self.nx), dtype=np.float64 if fp64 else np.float32)
-            _check(gg_read(self._sim, f, a.ctypes.data_as(_VP), 0, 1 if fp64 else 0), self._sim, "gg_read")
+        if out is None or isinstance(out, np.ndarray):
+            a = out if out is not None else np.empty((self.ny, self.nx), dtype=np.float64 if fp64 else np.float32)
+            assert a.flags.c_contiguous and a.size == self.nx * self.ny and a.dtype in (np.float32, np.float64)
+            is64 = a.dtype == np.float64
+            _check(gg_read(self._sim, f, a.ctypes.data_as(_VP), 0, 1 if is64 else 0), self._sim, "gg_read")
             return a
         import torch
         assert out.is_cuda and out.is_contiguous() and out.numel() == self.nx * self.ny

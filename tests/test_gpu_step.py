@@ -279,3 +279,19 @@ def test_hetero_8192_subsample_512():
     _, got = run_gpu(p, 5000, "fp32_kahan", steps_per_pass=3)
     for g, r in zip(got, ref):
         assert rel_err(g, r) <= 1e-5
+
+
+def test_read_into_caller_host_arrays():
+    """gg_read into a caller's host array (pageable or pinned, FP32 or FP64)
+    gives the same values as a fresh read."""
+    import torch
+    p = inputs.plain_128(100, 70, steps=30)
+    with gg.GGSim.from_problem(p, precision="fp32_kahan") as sim:
+        sim.step(30)
+        for f in ("u", "v", "w", "comp_v"):
+            ref32, ref64 = sim.read(f, fp64=False), sim.read(f)
+            a32 = np.empty((70, 100), dtype=np.float32)
+            assert sim.read(f, out=a32) is a32 and np.array_equal(a32, ref32)
+            pinned = torch.empty((70, 100), dtype=torch.float64).pin_memory().numpy()
+            sim.read(f, out=pinned)
+            assert np.array_equal(pinned, ref64)
