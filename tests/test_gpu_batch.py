@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from test_gpu_fullsize import window_oracle
 from paper_2006_01748_gb300 import build, gg, inputs
 
 pytestmark = pytest.mark.gpu
@@ -92,7 +93,23 @@ def test_full_ensemble_256_instances():
     probs = [inputs.ensemble_instance(k, specs[k]) for k in range(256)]
     with gg.GGBatch(probs) as b:
         b.autotune(trial_steps=8)
-        b.step(5000)
+        # sampled cells of sampled instances against the oracle on windows
+        # of half-width n + 2 (the light cone of n steps, as in
+        # test_gpu_fullsize.py), in the tuned launch configuration
+        n = 48
+        b.step(n)
+        rng = np.random.default_rng(4)
+        for k in (0, 100, 200, 255):
+            p = probs[k]
+            got = [b.read(k, f) for f in "uvw"]
+            scale = [max(float(np.max(np.abs(g))), 1e-300) for g in got]
+            pts = [(0, 0), (p.nx - 1, p.ny - 1), (p.nx // 2, p.ny // 2), (p.nx // 2 + int(0.1 * p.nx), p.ny // 2)]
+            pts += [(int(rng.integers(0, p.nx)), int(rng.integers(0, p.ny))) for _ in range(2)]
+            for i, j in pts:
+                ref = window_oracle(p, b.dt(k), i, j, n)
+                for g, r, sc in zip(got, ref, scale):
+                    assert abs(g[j, i] - r) <= 1e-5 * sc, (k, i, j)
+        b.step(5000 - n)
         info = b.launch_info()
         assert info["graph"], "the 5000-step launch should run as a replayed CUDA graph"
         assert info["tiles"] >= info["ctas"] > 0
