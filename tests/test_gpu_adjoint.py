@@ -68,6 +68,25 @@ def test_adjoint_matches_oracle(torch, nx, ny, steps):
         assert abs(got["scalars"][q] - ref["scalars"][q]) <= 1e-5 * max(abs(ref["scalars"][q]), 1e-12), q
 
 
+def test_adjoint_matches_oracle_on_rectangular_cells(torch):
+    """dx != dy (lx = 1, ly = 0.7 on 48 x 40 cells): every x / y factor of the
+    transpose and of the tensor gradients is exercised separately."""
+    nx, ny, steps = 48, 40, 150
+    p = small_problem(nx, ny, steps=steps)
+    p.lx, p.ly = 1.0, 0.7
+    Vstar = inputs.random_state(nx, ny, 98)[1]
+    dLdU = 1e-3 * inputs.white_noise(nx, ny, 17, -1, 1)
+    dLdW = 1e-3 * inputs.white_noise(nx, ny, 18, -1, 1)
+    ref = oracle_adjoint(p, steps, Vstar, dLdU, dLdW)
+    assert ref["s"].dx != ref["s"].dy
+    gV = oracle.misfit_grad(ref["V"], Vstar, ref["s"].dx, ref["s"].dy)
+    got = gpu_adjoint(torch, p, steps, dLdU, gV, dLdW)
+    for k in ("theta", "lambda1", "lambda2", "u0", "v0", "w0"):
+        assert rel_err(got[k], ref[k]) <= 1e-5, k
+    for q in range(4):
+        assert abs(got["scalars"][q] - ref["scalars"][q]) <= 1e-5 * max(abs(ref["scalars"][q]), 1e-12), q
+
+
 def test_adjoint_without_kahan_and_without_reactions(torch):
     nx, ny, steps = 48, 40, 100
     p = small_problem(nx, ny, steps=steps)
