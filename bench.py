@@ -35,6 +35,11 @@ if ROOT not in sys.path:
 
 METRIC = "cell-updates/s FP32 fused vs FP64 plain, % HBM roofline; adjoint/forward time"
 BYTES_PER_CELL_PASS = {"fp32_kahan": 60, "fp32": 36, "fp64": 72}
+# The method's FP32 flops per cell-step with each face flux evaluated once
+# (an FMA counts 2): tumour faces 2 x 6, acid faces 2 x 7, cross-term
+# differences and products 4, the two divergences 6, reactions 13, updates
+# 3 x 2 (Euler) or 3 x 5 (Kahan).
+FLOPS_PER_CELL_STEP = {"fp32": 55, "fp32_kahan": 64}
 
 
 def parse():
@@ -326,6 +331,18 @@ def run_ours(args, dist):
                 # (60 B per cell-update at the measured HBM bandwidth)
                 "t1_roof_cell_updates_per_s": peak * 1e9 / 60, "value_over_t1_roof": value / dist.world / (peak * 1e9 / 60)}
 
+    # the same step seen from the FP32 units: the method's flops per cell-step
+    # (each face flux evaluated once: tumour faces 2 x 6, acid faces 2 x 7 + 4
+    # per cell for the cross terms, divergences 6, reactions 13, Kahan updates
+    # 3 x 5) against the CUDA-core FP32 peak from unit counts and clock
+    # (152 SMs x 128 FP32 lanes x 2 flops per FMA x the SM clock under load)
+    sm_ghz = (ck.get("sm_mhz") or 2070.0) / 1e3
+    fp32_peak = 152 * 128 * 2 * sm_ghz / 1e3  # TFLOP/s
+    flops = FLOPS_PER_CELL_STEP["fp32_kahan"] * value / dist.world / 1e12
+    roofline_alu = {"bound": "alu", "achieved": flops, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": flops / fp32_peak, "flops_per_cell_step": FLOPS_PER_CELL_STEP["fp32_kahan"],
+                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % (sm_ghz * 1e3)}
+
     extras = {}
     if not args.no_extras:
         # the same step with one step per pass (the HBM-bound configuration)
@@ -436,7 +453,8 @@ def run_ours(args, dist):
             "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(p, args, T), "roofline": roofline, "cpu_baseline": cpu,
+            "config": workload_config(p, args, T), "roofline": roofline, "roofline_alu": roofline_alu,
+            "cpu_baseline": cpu,
             "cpu_baseline_omp": cpu_omp, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": ck, **extras,
         }
