@@ -321,12 +321,23 @@ int gg_batch_read(gg_batch* b, int32_t inst, int32_t field, void* dst,
 int gg_batch_diagnostics(gg_batch* b, int32_t inst, gg_diag* out);
 
 /* Autotuner of the ensemble launch: times trial_steps steps (>= 1; 0 means
- * 8) of every candidate tile shape -- steps per pass T in {1, 2, 3, 4} and
- * chunk height by in {32, 64, 128} rows (by >= 4T + 8) of the warp tiles,
- * whose strips are 32 - 2T columns wide -- on the batch itself, keeps the
- * fastest, and restores the state it advanced.  chosen (may be NULL)
- * receives {T, strip width, by, threads per CTA}.  Synchronizes. */
+ * 8) of every candidate -- the launch mode (the persistent cooperative
+ * kernel with a grid barrier between passes, or one launch of one warp per
+ * tile per pass), steps per pass T in {1, 2, 3, 4} and chunk height by in
+ * {32, 64, 128} rows (by >= 4T + 8) of the warp tiles, whose strips are
+ * 32 - 2T columns wide -- on the batch itself, keeps the fastest, and
+ * restores the state it advanced.  chosen (may be NULL) receives {T, strip
+ * width, by, threads per CTA (128: persistent mode, 32: passes mode)}.
+ * Synchronizes. */
 int gg_batch_autotune(gg_batch* b, int64_t trial_steps, int32_t* chosen);
+
+/* Sets the ensemble launch plan directly: passes_mode 0 runs the persistent
+ * cooperative kernel, 1 one launch per pass (one warp per tile, no grid
+ * barrier; a step of at most 4096 passes is captured into one CUDA graph,
+ * a longer one is launched directly); T in 1..4 steps per pass; chunk > 0
+ * rows per tile (0 means 64).  Every plan computes the same bits.  Returns
+ * GG_OK, GG_ERR_ARG or GG_ERR_OOM / GG_ERR_CUDA.  Synchronizes. */
+int gg_batch_set_plan(gg_batch* b, int32_t passes_mode, int32_t T, int32_t chunk);
 
 /* Testing hook for the bounded barrier wait: sets the per-wait time limit
  * (0 < seconds <= 60; 2 s by default) and, with extra_arrivals = 1, makes
@@ -338,11 +349,12 @@ int gg_batch_set_barrier_timeout(gg_batch* b, double seconds, int32_t extra_arri
 
 int32_t gg_batch_steps_per_pass(const gg_batch* b);
 
-/* Launch description of the last gg_batch_step: info[0..6] = steps per pass
- * T, strip width bx, chunk height by, threads per CTA, CTAs of the
- * persistent grid, work items (tiles) per pass, and 1 if the launch ran as a
- * replayed CUDA graph (0 if stream capture was refused and it was launched
- * directly). */
+/* Launch description of the last gg_batch_step: info[0..7] = steps per pass
+ * T, strip width bx, chunk height by, threads per CTA, CTAs of the grid
+ * (persistent mode: the persistent grid; passes mode: one per tile), work
+ * items (tiles) per pass, 1 if the launch ran as a replayed CUDA graph (0 if
+ * it was launched directly), and 1 for the passes mode (0 persistent).
+ * info must hold 8 int32. */
 int gg_batch_launch_info(const gg_batch* b, int32_t* info);
 double gg_batch_dt(const gg_batch* b, int32_t inst);
 const char* gg_batch_last_error(const gg_batch* b);

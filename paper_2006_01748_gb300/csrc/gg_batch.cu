@@ -104,6 +104,35 @@ __global__ void __launch_bounds__(128) batch_kernel(const InstDesc* __restrict__
     }
 }
 
+// One pass of T steps over every work item, one warp per item (the
+// "passes" mode: a graph of one launch per pass, no grid barrier; the kernel
+// boundary orders the passes).  Without the persistent loop the compiler
+// keeps fewer values in registers, so more warps fit on an SM.
+template <int T, bool KAHAN>
+__global__ void __launch_bounds__(32) pass_kernel(const InstDesc* __restrict__ desc, const int2* __restrict__ items,
+                                                  int nitems, int parity, int variant, int H)
+{
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const int2 it = items[w];
+    const InstDesc& d = desc[it.x];
+    const int strips = d.strips[variant];
+    stepw::warp_pass_any<T, KAHAN>(d.g[parity], d.r, H, it.y % strips, it.y / strips, threadIdx.x);
+}
+
+typedef void (*PassKernel)(const InstDesc*, const int2*, int, int, int, int);
+
+template <bool KAHAN>
+PassKernel pick_pass(int T)
+{
+    switch (T) {
+        case 1: return pass_kernel<1, KAHAN>;
+        case 2: return pass_kernel<2, KAHAN>;
+        case 3: return pass_kernel<3, KAHAN>;
+        default: return pass_kernel<4, KAHAN>;
+    }
+}
+
 typedef void (*BatchKernel)(const InstDesc*, const int2*, int, int, int, int, int, unsigned*, int*, unsigned,
                             unsigned long long);
 
@@ -119,6 +148,13 @@ BatchKernel pick(int T)
 }
 
 constexpr int kBatchMaxT = 4;
+// Launch modes of the ensemble (Plan32::kind): the persistent cooperative
+// kernel with a grid barrier between passes, or one launch per pass.
+constexpr int kModePersistent = 1;
+constexpr int kModePasses = 2;
+// A step of more passes than this in the passes mode is launched directly
+// instead of being captured into one graph.
+constexpr int64_t kMaxCapturedPasses = 4096;
 
 }  // namespace
 
@@ -239,6 +275,7 @@ BatchKernel kernel_for(const gg_batch* b, int T) { return b->kahan ? pick<true>(
 // kernel launches are enqueued.
 int prepare_kernels(gg_batch* b)
 {
+    if (b->plan.kind == kModePasses) return GG_OK;  // one CTA per work item, no persistent grid
     const int Ts[2] = {b->plan.T, 1};
     for (int v = 0; v < 2; ++v) {
         int ctas = 0;
@@ -254,6 +291,18 @@ int prepare_kernels(gg_batch* b)
 // (variant 0: the plan's T; variant 1: T = 1).
 int launch_passes(gg_batch* b, int T, int variant, int npasses, int parity0, cudaStream_t st)
 {
+    if (b->plan.kind == kModePasses) {
+        PassKernel pk = b->kahan ? pick_pass<true>(T) : pick_pass<false>(T);
+        const int nit = b->nitems[variant];
+        for (int p = 0; p < npasses; ++p) {
+            pk<<<std::max(nit, 1), 32, 0, st>>>(b->d_desc, b->d_items[variant], nit, (parity0 + p) & 1, variant,
+                                                b->plan.by);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return batch_fail(b, e, "batch pass launch");
+        }
+        b->ctas = nit;
+        return GG_OK;
+    }
     BatchKernel k = kernel_for(b, T);
     const int ctas = b->ctas_for_T[T];
     cudaLaunchConfig_t cfg = {};
@@ -429,7 +478,9 @@ int gg_batch_step(gg_batch* b, int64_t nsteps)
     const auto key = std::make_pair(nsteps, b->cur);
     auto it = b->graphs.find(key);
     cudaError_t e = cudaSuccess;
-    if (it == b->graphs.end() && b->cap_stream) {
+    const int64_t npass = nsteps / b->plan.T + nsteps % b->plan.T;
+    const bool capturable = b->plan.kind != kModePasses || npass <= kMaxCapturedPasses;
+    if (it == b->graphs.end() && b->cap_stream && capturable) {
         // Capture the launches of this (nsteps, parity) once on the private
         // stream, replay the graph on the caller's stream afterwards.
         cudaGraph_t graph = nullptr;
@@ -475,6 +526,7 @@ int gg_batch_launch_info(const gg_batch* b, int32_t* info)
     info[4] = b->ctas;
     info[5] = b->nitems[0];
     info[6] = b->captured ? 1 : 0;
+    info[7] = b->plan.kind == kModePasses ? 1 : 0;
     return GG_OK;
 }
 
@@ -546,13 +598,15 @@ int gg_batch_autotune(gg_batch* b, int64_t trial_steps, int32_t* chosen)
     for (auto& h : b->inst) maxnx = std::max(maxnx, h.nx);
     // Candidates: steps per pass and chunk height of the warp tiles.
     std::vector<Plan32> cands;
-    for (int T = 1; T <= kBatchMaxT; ++T)
-        for (int by : {32, 64, 128}) {
-            if (by < 4 * T + 8) continue;
-            Plan32 p;
-            p.kind = 1; p.T = T; p.halo = T; p.bx = 32 - 2 * T; p.by = by; p.threads = 128;
-            cands.push_back(p);
-        }
+    for (int mode : {kModePersistent, kModePasses})
+        for (int T = 1; T <= kBatchMaxT; ++T)
+            for (int by : {32, 64, 128}) {
+                if (by < 4 * T + 8) continue;
+                Plan32 p;
+                p.kind = mode; p.T = T; p.halo = T; p.bx = 32 - 2 * T; p.by = by;
+                p.threads = mode == kModePasses ? 32 : 128;
+                cands.push_back(p);
+            }
     // Tuning runs advance the state: save it and restore it afterwards.
     const int nstate = b->kahan ? 6 : 3;
     size_t bytes = 0;
@@ -612,6 +666,21 @@ int gg_batch_autotune(gg_batch* b, int64_t trial_steps, int32_t* chosen)
         chosen[0] = b->plan.T; chosen[1] = b->plan.bx; chosen[2] = b->plan.by; chosen[3] = b->plan.threads;
     }
     return rc;
+}
+
+int gg_batch_set_plan(gg_batch* b, int32_t passes_mode, int32_t T, int32_t chunk)
+{
+    if (!b) return GG_ERR_ARG;
+    if (T < 1 || T > kBatchMaxT || chunk < 0 || (passes_mode != 0 && passes_mode != 1)) {
+        b->last_error = "set_plan: T must be 1..4, chunk >= 0 and passes_mode 0 or 1";
+        return GG_ERR_ARG;
+    }
+    Plan32 p;
+    p.kind = passes_mode ? kModePasses : kModePersistent;
+    p.T = T; p.halo = T; p.bx = 32 - 2 * T;
+    p.by = chunk > 0 ? chunk : 64;
+    p.threads = passes_mode ? 32 : 128;
+    return configure(b, p);
 }
 
 int gg_batch_set_barrier_timeout(gg_batch* b, double seconds, int32_t extra_arrivals)

@@ -109,6 +109,7 @@ _SIGNATURES = {
     "gg_batch_set_barrier_timeout": (ctypes.c_int, [_VP, ctypes.c_double, _I32]),
     "gg_batch_steps_per_pass": (_I32, [_VP]),
     "gg_batch_launch_info": (ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
+    "gg_batch_set_plan": (ctypes.c_int, [_VP, _I32, _I32, _I32]),
     "gg_batch_last_error": (ctypes.c_char_p, [_VP]),
     "gg_batch_destroy": (ctypes.c_int, [_VP]),
 }
@@ -480,7 +481,8 @@ class GGBatch:
     def autotune(self, trial_steps: int = 8):
         chosen = (_I32 * 4)()
         self._check(lib().gg_batch_autotune(self._b, int(trial_steps), chosen), "gg_batch_autotune")
-        return dict(T=chosen[0], bx=chosen[1], by=chosen[2], threads=chosen[3])
+        return dict(T=chosen[0], bx=chosen[1], by=chosen[2], threads=chosen[3],
+                    mode="passes" if chosen[3] == 32 else "persistent")
 
     def step(self, nsteps: int):
         self._check(lib().gg_batch_step(self._b, int(nsteps)), "gg_batch_step")
@@ -489,10 +491,17 @@ class GGBatch:
         return lib().gg_batch_dt(self._b, inst)
 
     def launch_info(self) -> Dict:
-        info = (_I32 * 7)()
+        info = (_I32 * 8)()
         self._check(lib().gg_batch_launch_info(self._b, info), "gg_batch_launch_info")
         return dict(T=info[0], bx=info[1], by=info[2], threads=info[3], ctas=info[4], tiles=info[5],
-                    graph=bool(info[6]))
+                    graph=bool(info[6]), mode="passes" if info[7] else "persistent")
+
+    def set_plan(self, mode: str = "persistent", T: int = 1, chunk: int = 0):
+        """mode "persistent" (cooperative kernel, grid barrier between passes)
+        or "passes" (one launch of one warp per tile per pass)."""
+        assert mode in ("persistent", "passes")
+        self._check(lib().gg_batch_set_plan(self._b, 1 if mode == "passes" else 0, int(T), int(chunk)),
+                    "gg_batch_set_plan")
 
     def read(self, inst: int, field: str = "v", fp64: bool = True):
         p = self.problems[inst]

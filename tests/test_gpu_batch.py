@@ -30,13 +30,17 @@ def scaled_ensemble(n, scale, steps):
     return [inputs.ensemble_instance(k, specs[k], steps=steps, scale=scale) for k in range(n)]
 
 
-@pytest.mark.parametrize("spp", [1, 2, 4])
-def test_batch_matches_single_simulations_bitwise(spp):
+@pytest.mark.parametrize("mode", ["persistent", "passes"])
+@pytest.mark.parametrize("spp", [1, 2, 3, 4])
+def test_batch_matches_single_simulations_bitwise(spp, mode):
     probs = scaled_ensemble(12, 8, 37)
     with gg.GGBatch(probs, steps_per_pass=spp) as b:
+        b.set_plan(mode, spp, chunk=40)
         assert b.steps_per_pass == spp
         b.step(20)
         b.step(17)
+        info = b.launch_info()
+        assert info["mode"] == mode and info["T"] == spp
         for k, p in enumerate(probs):
             with gg.GGSim.from_problem(p, precision="fp32_kahan") as s:
                 assert b.dt(k) == s.dt
@@ -67,8 +71,23 @@ def test_autotune_restores_the_state():
         before = [b.read(k, "v") for k in range(6)]
         chosen = b.autotune(trial_steps=4)
         assert chosen["T"] in (1, 2, 3, 4) and chosen["bx"] == 32 - 2 * chosen["T"] and chosen["by"] > 0
+        assert chosen["mode"] in ("persistent", "passes")
         for k in range(6):
             assert np.array_equal(b.read(k, "v"), before[k])
+
+
+def test_long_step_in_passes_mode_is_launched_directly():
+    """More than 4096 passes in one step are not captured into one graph;
+    they run as direct launches and give the same bits."""
+    probs = scaled_ensemble(3, 16, 10)
+    with gg.GGBatch(probs, steps_per_pass=1) as a, gg.GGBatch(probs, steps_per_pass=1) as c:
+        a.set_plan("passes", 1, chunk=32)
+        a.step(4100)
+        assert a.launch_info()["graph"] is False
+        c.set_plan("persistent", 1, chunk=32)
+        c.step(4100)
+        for k in range(3):
+            assert np.array_equal(a.read(k, "v", fp64=False), c.read(k, "v", fp64=False))
 
 
 def test_barrier_wait_gives_up_and_reports_timeout():
