@@ -324,7 +324,7 @@ int gg_batch_diagnostics(gg_batch* b, int32_t inst, gg_diag* out);
  * 8) of every candidate -- the launch mode (the persistent cooperative
  * kernel with a grid barrier between passes, or one launch of one warp per
  * tile per pass), steps per pass T in {1, 2, 3, 4} and chunk height by in
- * {32, 64, 128} rows (by >= 4T + 8) of the warp tiles, whose strips are
+ * {32, 64, 128, 256} rows (by >= 4T + 8) of the warp tiles, whose strips are
  * 32 - 2T columns wide -- on the batch itself, keeps the fastest, and
  * restores the state it advanced.  chosen (may be NULL) receives {T, strip
  * width, by, threads per CTA (128: persistent mode, 32: passes mode)}.

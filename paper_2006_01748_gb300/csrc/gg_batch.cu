@@ -599,14 +599,16 @@ int gg_batch_autotune(gg_batch* b, int64_t trial_steps, int32_t* chosen)
     // Candidates: steps per pass and chunk height of the warp tiles.
     std::vector<Plan32> cands;
     for (int mode : {kModePersistent, kModePasses})
-        for (int T = 1; T <= kBatchMaxT; ++T)
-            for (int by : {32, 64, 128}) {
+        for (int T = 1; T <= kBatchMaxT; ++T) {
+            const std::vector<int> bys = {32, 64, 128, 256};
+            for (int by : bys) {
                 if (by < 4 * T + 8) continue;
                 Plan32 p;
                 p.kind = mode; p.T = T; p.halo = T; p.bx = 32 - 2 * T; p.by = by;
                 p.threads = mode == kModePasses ? 32 : 128;
                 cands.push_back(p);
             }
+        }
     // Tuning runs advance the state: save it and restore it afterwards.
     const int nstate = b->kahan ? 6 : 3;
     size_t bytes = 0;
