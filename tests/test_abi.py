@@ -90,5 +90,6 @@ def test_null_handles_are_rejected(lib):
     assert lib.gg_front_rays(None, 0, 0, 0.5, 0.5, 0.01, None) == gg.GG_ERR_ARG
     assert lib.gg_front_speed(None, 0, 0, 1, 0.5, 0.5, 0.01, None, None, None) == gg.GG_ERR_ARG
     assert lib.gg_adjoint_release(None) == gg.GG_ERR_ARG
+    assert lib.gg_batch_set_plan(None, 0, 1, 0) == gg.GG_ERR_ARG
     assert lib.gg_destroy(None) == gg.GG_OK
     assert lib.gg_dt(None) == 0.0
