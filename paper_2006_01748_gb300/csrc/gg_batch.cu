@@ -91,14 +91,25 @@ __global__ void __launch_bounds__(128) batch_kernel(const InstDesc* __restrict__
     unsigned gen = s_gen;
     const int lane = threadIdx.x & 31;
     const int wpc = blockDim.x >> 5;
+    // per warp: the grid and rates of its current item, staged in shared
+    // memory (read there by the pass instead of from the global descriptor)
+    __shared__ Grid32 sg[4];
+    __shared__ Rates32 sr[4];
+    const int wi = threadIdx.x >> 5;
     for (int pass = 0; pass < npasses; ++pass) {
         const int parity = (parity0 + pass) & 1;
-        for (int w = blockIdx.x * wpc + (threadIdx.x >> 5); w < nitems; w += gridDim.x * wpc) {
+        for (int w = blockIdx.x * wpc + wi; w < nitems; w += gridDim.x * wpc) {
             const int2 it = items[w];
             const InstDesc& d = desc[it.x];
             const int strips = d.strips[variant];
             const int sx = it.y % strips, sy = it.y / strips;
-            stepw::warp_pass_any<T, KAHAN, true>(d.g[parity], d.r, H, sx, sy, lane);
+            __syncwarp();  // every lane is done with the previous item's copy
+            const int* gsrc = reinterpret_cast<const int*>(&d.g[parity]);
+            const int* rsrc = reinterpret_cast<const int*>(&d.r);
+            for (int k = lane; k < (int)(sizeof(Grid32) / 4); k += 32) reinterpret_cast<int*>(&sg[wi])[k] = gsrc[k];
+            for (int k = lane; k < (int)(sizeof(Rates32) / 4); k += 32) reinterpret_cast<int*>(&sr[wi])[k] = rsrc[k];
+            __syncwarp();
+            stepw::warp_pass_any<T, KAHAN, true>(sg[wi], sr[wi], H, sx, sy, lane);
         }
         if (pass + 1 < npasses && !grid_barrier(bar, err, expected, gen, timeout_ns, &s_ok)) return;
     }
@@ -117,7 +128,18 @@ __global__ void __launch_bounds__(32) pass_kernel(const InstDesc* __restrict__ d
     const int2 it = items[w];
     const InstDesc& d = desc[it.x];
     const int strips = d.strips[variant];
-    stepw::warp_pass_any<T, KAHAN>(d.g[parity], d.r, H, it.y % strips, it.y / strips, threadIdx.x);
+    // the instance's grid and rates, staged in shared memory once: the pass
+    // reads its pointers and scalars from there instead of from the
+    // descriptor in global memory
+    __shared__ Grid32 sg;
+    __shared__ Rates32 sr;
+    static_assert(sizeof(Grid32) % 4 == 0 && sizeof(Rates32) % 4 == 0, "word copy");
+    const int* gsrc = reinterpret_cast<const int*>(&d.g[parity]);
+    const int* rsrc = reinterpret_cast<const int*>(&d.r);
+    for (int k = threadIdx.x; k < (int)(sizeof(Grid32) / 4); k += 32) reinterpret_cast<int*>(&sg)[k] = gsrc[k];
+    for (int k = threadIdx.x; k < (int)(sizeof(Rates32) / 4); k += 32) reinterpret_cast<int*>(&sr)[k] = rsrc[k];
+    __syncwarp();
+    stepw::warp_pass_any<T, KAHAN>(sg, sr, H, it.y % strips, it.y / strips, threadIdx.x);
 }
 
 typedef void (*PassKernel)(const InstDesc*, const int2*, int, int, int, int);

@@ -8,8 +8,8 @@
         the plain FP32 T = 1 plan, one line per plan on stdout
     python -m paper_2006_01748_gb300.prof adjoint --nx 2048 --steps 20 --T 3 --chunk 128
         one gg_adjoint call on the adjoint workload (forward plan fixed, no tuning)
-    python -m paper_2006_01748_gb300.prof batch --scale 1 --steps 6
-        the 256-instance ensemble, tuned, a few steps
+    python -m paper_2006_01748_gb300.prof batch --scale 1 --steps 6 [--mode passes --T 4 --chunk 128]
+        the 256-instance ensemble, tuned (or with the given plan), a few steps
 
 Each run synchronises and prints what it ran; nothing is timed here (time
 with CUDA events in bench.py, profile with ncu around these commands).
@@ -70,10 +70,14 @@ def _batch(args):
     specs = inputs.ensemble_specs(256)
     probs = [inputs.ensemble_instance(k, specs[k], scale=args.scale) for k in range(256)]
     with gg.GGBatch(probs) as b:
-        tuned = b.autotune(trial_steps=4)
+        if args.mode:
+            b.set_plan(args.mode, args.T, chunk=args.chunk)  # a fixed plan: no tuning launches
+            tuned = dict(mode=args.mode, T=args.T, by=args.chunk)
+        else:
+            tuned = b.autotune(trial_steps=4)
         b.step(args.steps)
         torch.cuda.synchronize()
-        print(f"batch tuned={tuned} steps={args.steps} info={b.launch_info()}", flush=True)
+        print(f"batch plan={tuned} steps={args.steps} info={b.launch_info()}", flush=True)
 
 
 def main(argv=None):
@@ -99,6 +103,9 @@ def main(argv=None):
     s = sub.add_parser("batch")
     s.add_argument("--scale", type=int, default=1)
     s.add_argument("--steps", type=int, default=6)
+    s.add_argument("--mode", default="", choices=["", "persistent", "passes"])
+    s.add_argument("--T", type=int, default=4)
+    s.add_argument("--chunk", type=int, default=128)
     s.set_defaults(fn=_batch)
     args = ap.parse_args(argv)
     args.fn(args)
