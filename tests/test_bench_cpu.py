@@ -71,3 +71,19 @@ def test_reference_arm_second_rank_exits_quietly():
                         "--steps", "1", "--warmup", "1"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_cpu_baseline_legs_on_a_small_grid():
+    """The one-core and the OpenMP baseline legs time the oracle on a bounded
+    sample and report what they ran on."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2006_01748_gb300 import inputs
+    p = inputs.hetero_8192(nx=96)
+    one = bench.cpu_baseline_leg(p)
+    assert one["kind"] == "oracle" and one["cores"] == 1 and one["value"] > 0
+    omp = bench.cpu_openmp_leg(p)
+    if omp is None:
+        pytest.skip("the compiler has no OpenMP")
+    assert omp["kind"] == "oracle (OpenMP build)" and omp["cores"] >= 1 and omp["value"] > 0
+    assert "explicit steps of the 96x96 grid" in omp["sample"]
