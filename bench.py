@@ -40,6 +40,12 @@ BYTES_PER_CELL_PASS = {"fp32_kahan": 60, "fp32": 36, "fp64": 72}
 # differences and products 4, the two divergences 6, reactions 13, updates
 # 3 x 2 (Euler) or 3 x 5 (Kahan).
 FLOPS_PER_CELL_STEP = {"fp32": 55, "fp32_kahan": 64}
+# The plain FP64 step's arithmetic per cell-step as step64_kernel writes it
+# (every face evaluated from both sides, an FMA counts 2): tumour faces
+# 4 x 5, their divergence 5, acid diagonal faces 4 x 3, tangential
+# differences 6, cross terms 4 x 3, the acid divergence 10, reactions 13,
+# Euler updates 3 x 2.
+FLOPS_PER_CELL_STEP_FP64 = 84
 
 
 def parse():
@@ -239,19 +245,95 @@ def cpu_openmp_leg(p):
             "sample": f"{n} explicit steps of the {p.nx}x{p.ny} grid ({el:.1f} s)"}
 
 
-def profiled_traffic(kernel_key: str, cells: int):
-    """DRAM bytes per launch of `kernel_key` from profiles/dram_traffic.txt
-    (one ncu capture, scaled to `cells` by the cells processed), or None."""
+def profiled_traffic(kind: str, T: int, prec: str, chunk: int, cells: int):
+    """DRAM bytes per launch of the plan (kind, T, prec) from
+    profiles/dram_traffic.txt (one ncu capture per plan on a 4096^2 grid),
+    at the captured chunk height nearest to `chunk`, scaled to `cells` by
+    the cells processed; None if the plan was not captured."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    best = None
     try:
         with open(path) as f:
             for line in f:
-                if line.startswith(kernel_key + " "):
-                    kv = dict(x.split("=") for x in line.split()[1:] if "=" in x)
-                    return int(kv["total"]) * cells / int(kv["cells"])
+                parts = line.split()
+                if len(parts) < 4 or line.startswith("#"):
+                    continue
+                if parts[0] != kind or parts[1] != f"T={T}" or parts[2] != prec:
+                    continue
+                kv = dict(x.split("=") for x in parts[3:] if "=" in x)
+                d = abs(int(kv["chunk"]) - chunk)
+                if best is None or d < best[0]:
+                    best = (d, int(kv["total"]) * cells / int(kv["cells"]))
     except (OSError, KeyError, ValueError):
-        pass
-    return None
+        return None
+    return None if best is None else best[1]
+
+
+def measured_alu_peaks():
+    """FMA rates measured on this GPU by the library's probe (flop/s):
+    FP64, FP32 scalar, FP32 packed pairs."""
+    from paper_2006_01748_gb300 import gg
+    out = {}
+    for name, kind, iters in (("fp64", 0, 20000), ("fp32", 1, 1000000), ("fp32x2", 2, 500000)):
+        best = 0.0
+        for _ in range(2):
+            rc, f = gg.gg_probe_fma_rate(kind, iters, 4)
+            if rc == gg.GG_OK:
+                best = max(best, f)
+        out[name] = best / 1e12
+    return out
+
+
+def error_leg():
+    """Measured relative max-norm errors against the FP64 oracle, outside the
+    timed region: the bench tissue's generator at 512 x 512 (same parameters,
+    grid-independent fields) for 5000 steps in each precision, per field; and
+    the adjoint workload's configuration at 128 x 128 for 10^4 steps (twin
+    target v-misfit), per gradient."""
+    import torch
+    import oracle
+    from paper_2006_01748_gb300 import gg, inputs
+
+    def rel(a, b):
+        return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+
+    out = {}
+    q = inputs.hetero_8192(nx=512, steps=5000)
+    lib = oracle.build_openmp()
+    if lib:
+        oracle.use_library(lib)  # same bits as the serial build, faster
+    try:
+        s, a = oracle.setup_for(q)
+        ref = oracle.run(s, *a, q.u0, q.v0, q.w0, q.steps)
+    finally:
+        oracle.use_library(None)
+    fwd = {}
+    for prec in ("fp64", "fp32_kahan", "fp32"):
+        with gg.GGSim.from_problem(q, precision=prec) as sim:
+            sim.step(q.steps)
+            got = sim.state()
+        fwd[prec] = {f: rel(g, r) for f, g, r in zip("uvw", got, ref)}
+    out["forward"] = {"workload": "hetero_8192 generator at 512x512, 5000 steps", **fwd}
+    p = inputs.adjoint_2048(nx=128, steps=10000)
+    tg = inputs.adjoint_2048(nx=128, steps=10000, target=True)
+    s, a = oracle.setup_for(p)
+    st, at = oracle.setup_for(tg, dt=s.dt)
+    Vs = oracle.run(st, *at, tg.u0, tg.v0, tg.w0, p.steps)[1]
+    V = oracle.run(s, *a, p.u0, p.v0, p.w0, p.steps)[1]
+    gV = oracle.misfit_grad(V, Vs, s.dx, s.dy)
+    z = np.zeros_like(V)
+    lam0, ga, gs = oracle.adjoint(s, *a, p.u0, p.v0, p.w0, p.steps, z, gV, z)
+    gth, gl1, gl2 = oracle.coefficients_vjp(p.theta, p.lambda1, p.lambda2, *ga)
+    with gg.GGSim.from_problem(p, precision="fp32_kahan", dt=s.dt) as sim:
+        r = sim.adjoint(p.steps, None, torch.from_numpy(gV.astype(np.float32)).cuda().view(-1), None)
+    adj = {k: rel(r[k].cpu().numpy().astype(np.float64), ref) for k, ref in
+           (("theta", gth), ("lambda1", gl1), ("lambda2", gl2), ("u0", lam0[0]), ("v0", lam0[1]), ("w0", lam0[2]))}
+    for qq, name in enumerate(("delta", "rho", "D", "c")):
+        adj[name] = abs(r["scalars"][qq] - gs[qq]) / abs(gs[qq])
+    out["adjoint"] = {"workload": "adjoint_2048 configuration at 128x128, 10^4 steps, twin-target v-misfit",
+                      "precision": "fp32_kahan", **adj}
+    out["metric"] = "max|F_gpu - F_oracle| / max|F_oracle| (rate gradients: relative difference)"
+    return out
 
 
 def timed_steps(sim, n, stream):
@@ -318,11 +400,13 @@ def run_ours(args, dist):
     peak, peak_kind = measured_peaks()
     if plan["kind"] == "warp":
         kname = "stepw1_kernel<Kahan>" if T == 1 else f"stepw_kernel<T={T},Kahan>"
+    elif plan["kind"] == "warp2":
+        kname = "stepw2_1_kernel<Kahan>" if T == 1 else f"stepw2_kernel<T={T},Kahan>"
     else:
         kname = f"step32_kernel<T={T},Kahan>"
     alg_bytes = BYTES_PER_CELL_PASS["fp32_kahan"] * p.cells
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
-    traffic = profiled_traffic(f"{plan['kind']} T={T} kahan chunk={plan['by']}", p.cells)
+    traffic = profiled_traffic(plan["kind"], T, "kahan", plan["by"], p.cells)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": kname, "chunk_rows": plan["by"],
                 "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": launch_ms,
@@ -341,7 +425,8 @@ def run_ours(args, dist):
     flops = FLOPS_PER_CELL_STEP["fp32_kahan"] * value / dist.world / 1e12
     roofline_alu = {"bound": "alu", "achieved": flops, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": flops / fp32_peak, "flops_per_cell_step": FLOPS_PER_CELL_STEP["fp32_kahan"],
-                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % (sm_ghz * 1e3)}
+                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz (the measured FMA-chain rate "
+                                 "is in alu_peaks_tflops)" % (sm_ghz * 1e3)}
 
     extras = {}
     if not args.no_extras:
@@ -357,19 +442,30 @@ def run_ours(args, dist):
             ach2 = bpc * p.cells / (ms2 / 1e3 / n2) / 1e9
             extras[name] = {"value": p.cells * n2 / (ms2 / 1e3), "unit": "cell-updates/s",
                             "roofline": {"bound": "hbm", "achieved": ach2, "peak": peak, "unit": "GB/s",
-                                         "frac": ach2 / peak, "kernel": f"stepw1_kernel<{prec}>",
+                                         "frac": ach2 / peak,
+                                         "kernel": f"{'stepw2_1_kernel' if pl2['kind'] == 'warp2' else 'stepw1_kernel'}"
+                                                   f"<{prec}>",
                                          "chunk_rows": pl2["by"],
-                                         "traffic": profiled_traffic(f"warp T=1 {'kahan' if prec == 'fp32_kahan' else 'plain'}"
-                                                                     f" chunk={pl2['by']}", p.cells)}}
+                                         "traffic": profiled_traffic(pl2["kind"], 1, "kahan" if prec == "fp32_kahan"
+                                                                     else "plain", pl2["by"], p.cells)}}
         # plain FP64 step on the same grid (fewer time steps; throughput is per cell-update)
         sim64 = gg.GGSim.from_problem(p, precision="fp64")
         sim64.step(5)
         ms64 = timed_steps(sim64, args.fp64_time_steps, stream)
         sim64.close()
         v64 = p.cells * args.fp64_time_steps / (ms64 / 1e3)
+        alu = measured_alu_peaks()
+        fl64 = FLOPS_PER_CELL_STEP_FP64 * v64 / 1e12
         extras["fp64_plain"] = {"value": v64, "unit": "cell-updates/s", "time_steps": args.fp64_time_steps,
+                                "kernel": "step64_kernel",
+                                "roofline": {"bound": "alu", "achieved": fl64, "peak": alu["fp64"],
+                                             "unit": "TFLOP/s", "frac": fl64 / alu["fp64"] if alu["fp64"] else None,
+                                             "flops_per_cell_step": FLOPS_PER_CELL_STEP_FP64,
+                                             "peak_kind": "measured: FP64 FMA chains (gg_probe_fma_rate)"},
                                 "hbm_frac": 72 * p.cells / (ms64 / 1e3 / args.fp64_time_steps) / 1e9 / peak,
                                 "fp32_over_fp64": value / dist.world / v64}
+        extras["alu_peaks_tflops"] = {**alu, "how": "gg_probe_fma_rate: 8 independent FMA chains per thread, "
+                                                    "4 waves of 256-thread CTAs, CUDA events"}
         # adjoint / forward on the 2048 x 2048 adjoint workload (10^4 steps,
         # sqrt(N) checkpointing): the forward solve as gg_step runs it (tuned
         # plan), and the whole gg_adjoint call (its own forward pass, the
@@ -422,6 +518,9 @@ def run_ours(args, dist):
                               "cells": ens_cells, "value": ens_cells * args.ensemble_steps / (ens_ms / 1e3),
                               "unit": "cell-updates/s", "plan": tuned, "graph": info["graph"], "ctas": info["ctas"],
                               "hbm_frac": 60 * ens_cells * args.ensemble_steps / tuned["T"] / (ens_ms / 1e3) / 1e9 / peak}
+        # measured per-field / per-gradient errors against the FP64 oracle (outside the timed region)
+        if dist.rank == 0:
+            extras["errors"] = error_leg()
 
     # end to end through the public API with host buffers in pinned memory:
     # every step creates the simulation from the host arrays (H2D: tensor

@@ -1,11 +1,12 @@
 """Small, self-contained runs of single kernels, for profilers.
 
-    python -m paper_2006_01748_gb300.prof step --nx 4096 --kind warp --T 3 --chunk 128
+    python -m paper_2006_01748_gb300.prof step --nx 4096 --kind warp2 --T 4 --chunk 128
         3 passes of the FP32 step with that plan on the heterogeneous tissue
-        (capture the third: ``ncu -k regex:stepw -s 2 -c 1 ...``)
+        (capture the third: ``ncu --clock-control none -k regex:stepw -s 2 -c 1 ...``)
     python -m paper_2006_01748_gb300.prof plans --nx 4096
-        3 passes of each warp plan (T = 1..4, chunks 64/128/256, Kahan) and of
-        the plain FP32 T = 1 plan, one line per plan on stdout
+        3 passes of each warp plan, one and two columns per lane (T = 1..4,
+        chunks 64/128/256, Kahan) and of the plain FP32 T = 1 plans, one line
+        per plan on stdout
     python -m paper_2006_01748_gb300.prof adjoint --nx 2048 --steps 20 --T 3 --chunk 128
         one gg_adjoint call on the adjoint workload (forward plan fixed, no tuning)
     python -m paper_2006_01748_gb300.prof batch --scale 1 --steps 6 [--mode passes --T 4 --chunk 128]
@@ -39,7 +40,8 @@ def _plans(args):
     build()
     p = inputs.hetero_8192(nx=args.nx)
     plans = [("warp", T, "fp32_kahan", c) for T in (1, 2, 3, 4) for c in (64, 128, 256)]
-    plans += [("warp", 1, "fp32", 64), ("warp", 1, "fp32", 128)]
+    plans += [("warp2", T, "fp32_kahan", c) for T in (1, 2, 3, 4) for c in (64, 128, 256)]
+    plans += [("warp", 1, "fp32", 64), ("warp", 1, "fp32", 128), ("warp2", 1, "fp32", 64), ("warp2", 1, "fp32", 128)]
     for kind, T, prec, chunk in plans:
         with gg.GGSim.from_problem(p, precision=prec, steps_per_pass=1) as sim:
             sim.set_plan(kind, T, chunk=chunk)
@@ -85,7 +87,7 @@ def main(argv=None):
     sub = ap.add_subparsers(dest="cmd", required=True)
     s = sub.add_parser("step")
     s.add_argument("--nx", type=int, default=4096)
-    s.add_argument("--kind", default="warp", choices=["warp", "smem"])
+    s.add_argument("--kind", default="warp", choices=["warp", "warp2", "smem"])
     s.add_argument("--T", type=int, default=1)
     s.add_argument("--chunk", type=int, default=0)
     s.add_argument("--passes", type=int, default=3)
