@@ -113,7 +113,7 @@ struct AdjCarry {
     float LxE = 0.f, LxW = 0.f;  // lamW differences across the east / west faces of row q
     float Sx = 0.f, SxS = 0.f;   // b (LxE + LxW) of rows q and q-1
     float Ly = 0.f;              // lamW difference across the north face of row q-1
-    float h = 0.f, f = 0.f, e = 0.f, g = 0.f, qq = 0.f;  // north-face terms of row q-1 (below)
+    float f = 0.f, e = 0.f, g = 0.f, qq = 0.f;  // north-face terms of row q-1 (below)
 };
 
 // One adjoint step at row q of one lane, from the state and lam of rows P (q)
@@ -122,11 +122,16 @@ struct AdjCarry {
 // the warp call it (it shuffles).  Face terms, each with the factor 1/h^2 of
 // its direction: with m = 1 - (U_P + U_nb)/2, dv = V_nb - V_P, dl the
 // compensated difference of lamV (neighbour minus own),
-//   h = m dv (D1 of V),  f = m dl (D1^T of lamV),  e = dv dl (dD1/dU),
+//   f = m dl (D1^T of lamV),  e = dv dl (dD1/dU),
 // the east / north terms are computed here, the west ones are the west
 // lane's east ones and the south ones the carried north ones of row q-1:
-//   D1 = (hE - hW) + (hN - hS),  D1^T = (fE - fW) + (fN - fS),
-//   dD1/dU = (eE + eW + eN + eS) / 2.
+//   D1^T = (fE - fW) + (fN - fS),  dD1/dU = (eE + eW + eN + eS) / 2.
+// The rate term of D, sum_cells lamV D1(V; U), is taken in its transposed
+// form sum_cells V D1^T(lamV; U): D1(.; U) is a symmetric matrix (Table 1's
+// face fluxes with zero flux through boundary faces), so the two sums are
+// equal, and the second needs no second difference of the FP32 state V
+// (whose rounding, divided by h^2, swamps the smooth part of D1(V) on fine
+// grids) but only the compensated differences of lamV.
 template <bool KAHAN, bool EDGE, bool YEDGE = true>
 __device__ __forceinline__ AdjOut adj_level(const Rates32& k, float Sw, const AdjRow& P, const AdjRow& N, float lu,
                                             float clu, float ax, bool hasW, bool hasE, bool hasS_, bool hasN_,
@@ -171,12 +176,11 @@ __device__ __forceinline__ AdjOut adj_level(const Rates32& k, float Sw, const Ad
     const float mE = 1.0f - 0.5f * (P.u + uE), mN = 1.0f - 0.5f * (P.u + uN);
     const float dvE = (vE - P.v) * k.ihx2, dvN = (vN - P.v) * k.ihy2;
     const float dlE = dW(lvE, cvE, P.lv, P.clv), dlN = hasN ? dW(N.lv, N.clv, P.lv, P.clv) : 0.0f;
-    const float hE = mE * dvE, fE = mE * dlE * k.ihx2, eE = dvE * dlE;
-    const float hN = mN * dvN, fN = mN * dlN * k.ihy2, eN = dvN * dlN;
-    float hW = from_west(hE), fW = from_west(fE), eW = from_west(eE);
-    if (EDGE && !hasW) { hW = 0.0f; fW = 0.0f; eW = 0.0f; }
-    const float hS = hasS ? c.h : 0.0f, fS = hasS ? c.f : 0.0f, eS = hasS ? c.e : 0.0f;
-    const float d1 = (hE - hW) + (hN - hS);
+    const float fE = mE * dlE * k.ihx2, eE = dvE * dlE;
+    const float fN = mN * dlN * k.ihy2, eN = dvN * dlN;
+    float fW = from_west(fE), eW = from_west(eE);
+    if (EDGE && !hasW) { fW = 0.0f; eW = 0.0f; }
+    const float fS = hasS ? c.f : 0.0f, eS = hasS ? c.e : 0.0f;
     const float d1T = (fE - fW) + (fN - fS);
     const float dU = 0.5f * ((eE + eW) + (eN + eS));
 
@@ -195,7 +199,7 @@ __device__ __forceinline__ AdjOut adj_level(const Rates32& k, float Sw, const Ad
         o.s_rho = P.lv * P.v * (1.0f - P.v);
         o.s_c = P.lw * (P.v - P.w);
     }
-    o.s_D = P.lv * d1;
+    o.s_D = P.v * d1T;
     if (KAHAN) {
         kahan_add(lu, k.dt * fu, clu, o.lu, o.clu);
         kahan_add(P.lv, k.dt * fvv, P.clv, o.lv, o.clv);
@@ -214,12 +218,17 @@ __device__ __forceinline__ AdjOut adj_level(const Rates32& k, float Sw, const Ad
     c.LxE = LxE_N; c.LxW = LxW_N;
     c.SxS = SxP; c.Sx = SxN;
     c.Ly = LyN;
-    c.h = hN; c.f = fN; c.e = eN; c.g = gN; c.qq = qN;
+    c.f = fN; c.e = eN; c.g = gN; c.qq = qN;
     return o;
 }
 
-// Per-lane FP32 Kahan sums of the four rate terms, folded into one FP64
-// record per warp at the end of the chunk (fixed order).
+// Per-lane FP32 compensated sums of the four rate terms, folded into one
+// FP64 record per warp at the end of the chunk (fixed order).  delta, rho and
+// c use Kahan's update; the D term, V D1^T(lamV), sums to a small fraction of
+// the sum of its magnitudes (D1^T(lamV) sums to zero over the domain), so it
+// keeps the exact rounding error of every addition (TwoSum) in a second
+// accumulator: the result is then accurate to about one FP32 rounding of the
+// sum itself rather than of the sum of magnitudes.
 struct RateSums {
     float acc[4] = {0.f, 0.f, 0.f, 0.f}, accc[4] = {0.f, 0.f, 0.f, 0.f};
     __device__ __forceinline__ void add(int q, float x)
@@ -229,11 +238,21 @@ struct RateSums {
         accc[q] = __fsub_rn(__fsub_rn(t, acc[q]), y);
         acc[q] = t;
     }
+    // acc + x = s + e exactly (TwoSum); e is gathered in -accc (so that the
+    // fold below, acc - accc, stays the same for both kinds of sum)
+    __device__ __forceinline__ void add_two_sum(int q, float x)
+    {
+        const float s = __fadd_rn(acc[q], x);
+        const float z = __fsub_rn(s, acc[q]);
+        const float e = __fadd_rn(__fsub_rn(acc[q], __fsub_rn(s, z)), __fsub_rn(x, z));
+        accc[q] = __fsub_rn(accc[q], e);
+        acc[q] = s;
+    }
     __device__ __forceinline__ void add_all(const AdjOut& o)
     {
         add(0, o.s_delta);
         add(1, o.s_rho);
-        add(2, o.s_D);
+        add_two_sum(2, o.s_D);
         add(3, o.s_c);
     }
     __device__ __forceinline__ void fold(double* part, int lane, float dt)
@@ -623,6 +642,10 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
         s->last_error = "the adjoint is provided for the FP32 precisions";
         return GG_ERR_STATE;
     }
+    if (s->params.adapt_every > 0) {
+        s->last_error = "the adjoint holds dt fixed: not available with the adaptive step";
+        return GG_ERR_STATE;
+    }
     const bool kahan = s->params.precision == GG_FP32_KAHAN;
     const int64_t N = nsteps;
     int K = (int)(checkpoint_every > 0 ? checkpoint_every : (int64_t)ceil(sqrt((double)std::max<int64_t>(N, 1))));
@@ -640,8 +663,10 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
     const Rates32 r = rates32(s);
     // recompute depth and chunk height: the simulation's warp plan when it has
     // one, else single steps
-    const int TR = s->plan.kind == 1 ? s->plan.T : 1;
-    const int HR = s->plan.kind == 1 ? s->plan.by : default_plan(s->nx, s->ny, 1).by;
+    const bool warp_plan = s->plan.kind == 1 || s->plan.kind == 3;
+    const int TR = warp_plan ? s->plan.T : 1;
+    const int HR = warp_plan ? s->plan.by : default_plan(s->nx, s->ny, 1).by;
+    const bool paired = s->plan.kind == 3;
     // Runs nsteps steps from the state `in` (u, v, w, cu, cv, cw) in passes of
     // up to TR steps.  The state after step kk (1 <= kk < nsteps, and nsteps
     // itself when fin is null) is written to slot(kk) (u, v, w); the last
@@ -676,7 +701,7 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
                 float* const* x = slot(kk + t);
                 sh.u[t - 1] = x[0]; sh.v[t - 1] = x[1]; sh.w[t - 1] = x[2];
             }
-            ee = launch_stepw_stash(g, r, HR, Tp, kahan, sh, st);
+            ee = paired ? launch_stepw2_stash(g, r, HR, Tp, kahan, sh, st) : launch_stepw_stash(g, r, HR, Tp, kahan, sh, st);
             kk += Tp;
             ++pass;
         }

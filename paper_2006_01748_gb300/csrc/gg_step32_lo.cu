@@ -32,6 +32,7 @@ cudaError_t launch_step32(const Grid32& g, const Rates32& r, const Plan32& p, in
 cudaError_t launch_plan(const Grid32& g, const Rates32& r, const Plan32& p, int T, bool kahan, cudaStream_t s)
 {
     if (p.kind == 1 && T <= 4) return launch_stepw(g, r, p.by, T, kahan, s);
+    if (p.kind == 3 && T <= 4) return launch_stepw2(g, r, p.by, T, kahan, s);
     Plan32 q = p;
     if (q.halo < T) q.halo = T;
     return launch_step32(g, r, q, T, kahan, s);

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(32) stepw_kernel(const Grid32 g, const Rates32
     const int gw = blockIdx.x;
     if (gw >= nwarps) return;
     const int strip = gw % nstrips, chunk = gw / nstrips;
-    stepw::warp_pass_any<T, KAHAN>(g, k, H, strip, chunk, lane);
+    stepw::warp_pass_any<T, KAHAN>(g, live_rates(k), H, strip, chunk, lane);
 }
 
 // The one-step pass needs occupancy to hide HBM latency: 4-warp CTAs, bound
@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(128, KAHAN ? 6 : 8) stepw1_kernel(const Grid32
     const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (gw >= nwarps) return;  // whole warps only
     const int strip = gw % nstrips, chunk = gw / nstrips;
-    stepw::warp_pass_any<1, KAHAN>(g, k, H, strip, chunk, lane);
+    stepw::warp_pass_any<1, KAHAN>(g, live_rates(k), H, strip, chunk, lane);
 }
 
 template <int T, bool KAHAN>
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(32) stepw_stash_kernel(const Grid32 g, const R
     const int gw = blockIdx.x;
     if (gw >= nwarps) return;
     const int strip = gw % nstrips, chunk = gw / nstrips;
-    stepw::warp_pass_any<T, KAHAN, false, true>(g, k, H, strip, chunk, lane, &st);
+    stepw::warp_pass_any<T, KAHAN, false, true>(g, live_rates(k), H, strip, chunk, lane, &st);
 }
 
 template <int T, bool KAHAN>

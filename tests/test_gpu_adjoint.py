@@ -201,30 +201,50 @@ def _fp64_loss_vw(p, dt, steps, Vstar, **over):
     return (0.5 * float(np.sum((V - Vstar) ** 2)) + float(np.sum(W))) / p.cells
 
 
+def _twin_misfit_seed(p, tgt, dt, steps):
+    """V* of the twin run (tensor from seed + 1) and dL/dV^N of the v-misfit,
+    both from FP64 forward runs with the fixed dt (so the seed given to the
+    adjoint is the one the finite differences of the FP64 loss see)."""
+    with gg.GGSim.from_problem(tgt, precision="fp64", dt=dt) as sim:
+        sim.step(steps)
+        Vstar = sim.read("v")
+    with gg.GGSim.from_problem(p, precision="fp64", dt=dt) as sim:
+        sim.step(steps)
+        V = sim.read("v")
+    return Vstar, (V - Vstar) / p.cells
+
+
 def test_adjoint_2048_rate_gradients_against_finite_differences(torch):
     """Full-size adjoint workload (2048 x 2048, 10^4 steps, sqrt(N)
     checkpointing).  Over its short physical time (t = 10^4 dt, about 5e-4)
     the v-misfit alone has gradients near 1e-20, so the checked loss adds the
-    acid mass: L = dx dy [ sum (V - V*)^2 / 2 + sum W ].  Its gradients for the
-    rates c and delta are compared with central differences of the GPU FP64
-    forward (dt held fixed)."""
+    acid mass: L = dx dy [ sum (V - V*)^2 / 2 + sum W ].  Its seeds dL/dX^N are
+    taken from the FP64 forward (the misfit V - V* is small enough that the
+    FP32 forward's rounding would change it), and the FP32 adjoint's rate
+    gradients are compared with central differences of the GPU FP64 forward
+    (dt held fixed).
+
+    Measured: c 8e-9, rho 5e-7, delta within the rounding floor of the
+    central difference, D 1.5e-3.  The D gradient is held to 2e-3: over this
+    workload's physical time (sqrt(D t) is a third of a cell) a 100 % change
+    of D moves L by about 1e-7 of itself, so its gradient is a sum of
+    per-cell terms lamV D1(V; U) that cancel to a small fraction of their
+    magnitudes, and the FP32 state and sums leave it that accurate.  The same
+    gradient matches the FP64 oracle to 6e-8 on the 128^2 grid over 10^4
+    steps (test_adjoint_10k_steps_matches_oracle)."""
     p = inputs.adjoint_2048()
     tgt = inputs.adjoint_2048(target=True)
-    with gg.GGSim.from_problem(tgt, precision="fp32_kahan") as sim:
-        sim.step(p.steps)
-        Vstar = sim.read("v")
     with gg.GGSim.from_problem(p, precision="fp64") as sim:
         dt = sim.dt
+    Vstar, gV = _twin_misfit_seed(p, tgt, dt, p.steps)
     with gg.GGSim.from_problem(p, precision="fp32_kahan", dt=dt) as sim:
-        sim.step(p.steps)
-        V = sim.read("v")
-    with gg.GGSim.from_problem(p, precision="fp32_kahan", dt=dt) as sim:
-        tv = torch.from_numpy(((V - Vstar) / p.cells).astype(np.float32)).cuda().view(-1)
+        tv = torch.from_numpy(gV.astype(np.float32)).cuda().view(-1)
         tw = torch.full((p.cells,), 1.0 / p.cells, dtype=torch.float32, device="cuda")
         r = sim.adjoint(p.steps, None, tv, tw, outputs=("theta",))
         assert sim.steps == p.steps
     assert np.all(np.isfinite(r["theta"].cpu().numpy()))
     L0 = _fp64_loss_vw(p, dt, p.steps, Vstar)
+    bad = []
     for q, name in ((3, "c"), (2, "D"), (1, "rho"), (0, "delta")):
         h = 1e-3 * getattr(p, name)
         fd = (_fp64_loss_vw(p, dt, p.steps, Vstar, **{name: getattr(p, name) + h})
@@ -232,12 +252,54 @@ def test_adjoint_2048_rate_gradients_against_finite_differences(torch):
         noise = 1e-15 * abs(L0) / h   # rounding floor of the central difference
         if name == "c":
             assert abs(fd) > 1e3 * noise   # the acid rate carries the signal
-        # FP32 second differences of V at h = 1/2048 lose about 11 bits to
-        # cancellation in smooth regions, so the gradients driven by D1 (D,
-        # rho, delta through U) carry ~1e-3 relative error after 10^4 steps;
-        # the acid-driven gradient stays within 1e-4.
-        tol = 1e-4 if name == "c" else 3e-3
-        assert abs(fd - r["scalars"][q]) <= tol * abs(fd) + 10 * noise, (name, fd, r["scalars"][q], noise)
+        print(f"{name}: fd {fd:.12e} adjoint {r['scalars'][q]:.12e} rel {abs(fd - r['scalars'][q]) / abs(fd):.3e}")
+        tol = 2e-3 if name == "D" else 1e-5
+        if abs(fd - r["scalars"][q]) > tol * abs(fd) + 10 * noise:
+            bad.append((name, fd, r["scalars"][q], noise))
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("loss", ["v_misfit", "v_misfit_plus_w_mass"])
+def test_adjoint_10k_steps_matches_oracle(torch, loss):
+    """The adjoint workload's rates, tensor field, twin target and step count
+    (10^4 steps, sqrt(N) checkpointing) on a 128 x 128 grid, where the
+    oracle's store-all FP64 adjoint fits in host memory (3.9 GB of states).
+    Every output -- dL/d(theta, lambda1, lambda2), dL/d(U, V, W) at step 0
+    and the four rate gradients -- is compared element by element with the
+    oracle, both sides given the same seeds (the oracle's dL/dX^N).
+
+    v_misfit is the configured loss L = dx dy sum (V^N - V*)^2 / 2: every
+    output is held to 1e-5.  v_misfit_plus_w_mass adds dx dy sum W^N, a
+    uniform source for lambda_W: the tensor gradients then come from
+    differences of nearly equal lambda_W values, which keep the FP32 rounding
+    of the increments c lambda_W dt (about 1e-3 lambda_W per step); they are
+    held to 2e-5, the other outputs to 1e-5."""
+    nx, steps = 128, 10000
+    p = inputs.adjoint_2048(nx=nx, steps=steps)
+    tg = inputs.adjoint_2048(nx=nx, steps=steps, target=True)
+    s, a = oracle.setup_for(p)
+    st, at = oracle.setup_for(tg, dt=s.dt)
+    Vstar = oracle.run(st, *at, tg.u0, tg.v0, tg.w0, steps)[1]
+    V = oracle.run(s, *a, p.u0, p.v0, p.w0, steps)[1]
+    gV = oracle.misfit_grad(V, Vstar, s.dx, s.dy)
+    gW = np.full_like(V, s.dx * s.dy) if loss == "v_misfit_plus_w_mass" else np.zeros_like(V)
+    z = np.zeros_like(V)
+    lam0, ga, gs = oracle.adjoint(s, *a, p.u0, p.v0, p.w0, steps, z, gV, gW)
+    gth, gl1, gl2 = oracle.coefficients_vjp(p.theta, p.lambda1, p.lambda2, *ga)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda().view(-1)
+    with gg.GGSim.from_problem(p, precision="fp32_kahan", dt=s.dt) as sim:
+        r = sim.adjoint(steps, None, t(gV), t(gW) if loss != "v_misfit" else None)
+        assert sim.steps == steps
+    tensor_tol = 1e-5 if loss == "v_misfit" else 2e-5
+    for k, ref, tol in (("theta", gth, tensor_tol), ("lambda1", gl1, tensor_tol), ("lambda2", gl2, tensor_tol),
+                        ("u0", lam0[0], 1e-5), ("v0", lam0[1], 1e-5), ("w0", lam0[2], 1e-5)):
+        err = rel_err(r[k].cpu().numpy().astype(np.float64), ref)
+        print(f"{loss} {k}: {err:.3e}")
+        assert err <= tol, (k, err)
+    for q in range(4):
+        err = abs(r["scalars"][q] - gs[q]) / abs(gs[q])
+        print(f"{loss} scalar {q}: {err:.3e}")
+        assert err <= 1e-5, (q, r["scalars"][q], gs[q])
 
 
 def test_autograd_function(torch):

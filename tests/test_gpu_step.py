@@ -67,7 +67,8 @@ def test_ragged_and_degenerate_grids(nx, ny, precision):
         assert rel_err(g, r) <= TOL[precision], name
 
 
-PLANS = [("warp", T) for T in (1, 2, 3, 4)] + [("smem", T) for T in range(1, 9)]
+PLANS = ([("warp", T) for T in (1, 2, 3, 4)] + [("warp2", T) for T in (1, 2, 3, 4)]
+         + [("smem", T) for T in range(1, 9)])
 
 
 @pytest.mark.parametrize("kind,T", PLANS)
@@ -104,6 +105,27 @@ def test_every_plan_is_bitwise_identical(precision):
             else:
                 for g, b in zip(got, base):
                     assert np.array_equal(g, b), (kind, T, chunk)
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 6), (5, 1), (3, 5), (77, 45), (131, 29), (64, 33)])
+def test_paired_column_plans_on_ragged_grids(nx, ny):
+    """The paired-column kernel on odd widths (its last pair reads one column
+    of the row only), widths below one strip and single rows or columns:
+    every T and chunk height gives the bits of the one-column kernel."""
+    p = inputs.plain_128(nx, ny, steps=13)
+    p.u0, p.v0, p.w0 = inputs.random_state(nx, ny, 3 + nx + ny)
+    with gg.GGSim.from_problem(p, precision="fp32_kahan") as sim:
+        sim.set_plan("warp", 1)
+        sim.step(p.steps)
+        base = sim.state(fp64=False)
+    for T in (1, 2, 3, 4):
+        for chunk in (0, 7):
+            with gg.GGSim.from_problem(p, precision="fp32_kahan") as sim:
+                sim.set_plan("warp2", T, chunk=chunk)
+                assert sim.plan()["kind"] == "warp2"
+                sim.step(p.steps)
+                for g, b in zip(sim.state(fp64=False), base):
+                    assert np.array_equal(g, b), (T, chunk)
 
 
 def test_autotuner_keeps_the_state_and_the_bits():
