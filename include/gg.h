@@ -103,7 +103,8 @@ typedef struct {
     int32_t precision;     /* GG_FP64_PLAIN, GG_FP32 or GG_FP32_KAHAN */
     int32_t flags;         /* GG_FLAG_* */
     int32_t steps_per_pass;/* time steps per pass over HBM (temporal blocking), 0 = tuned */
-    int32_t reserved;      /* must be 0 */
+    int32_t adapt_every;   /* 0: fixed dt (below); n >= 1: adaptive Delta t_k recomputed
+                              on the device every n steps (below); dt must then be 0 */
 } gg_params;
 
 /* Stable-step rule (Section 2 recomputes dt for stability without giving a
@@ -111,7 +112,20 @@ typedef struct {
  *   dt_max = 1 / ( 2 Lambda (1/dx^2 + 1/dy^2) + c + rho + 1 + delta ),
  *   Lambda = max( max over cells of lambda_max(A), D ).
  * It keeps every diagonal coefficient of eq. (3) non-negative and is below
- * h^2 / (4 Lambda) on a square grid. */
+ * h^2 / (4 Lambda) on a square grid.
+ *
+ * Adaptive step (adapt_every = n >= 1; Section 2's Delta t_k recomputed from
+ * the state): at every step k = 0, n, 2n, ... counted from gg_create,
+ *   Delta t_k = cfl / max( c + 2 Lambda_A (1/dx^2 + 1/dy^2),
+ *                          max over cells of U + delta W - 1,
+ *                          max over cells of D S - rho (1 - V) ),
+ *   S = sum over the cell's interior faces f of (1 - (U_P + U_nb)/2) / h_f^2,
+ *   Lambda_A = max over cells of lambda_max(A),
+ * the largest step keeping the coefficient of each unknown's own old value in
+ * eq. (3) at least 1 - cfl (the reaction parts are left out with
+ * GG_FLAG_NO_REACTION).  It is reduced from the state on the device and read
+ * there by the step kernels: no host round trip.  The per-cell terms are
+ * evaluated in the state's precision. */
 
 typedef struct {
     double mass[3];      /* dx dy sum of U, V, W (finite values only) */
@@ -232,26 +246,29 @@ int gg_adjoint_release(gg_sim* sim);
 
 /* Diagnostics without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- code
- * running while its stream is captured into a CUDA graph, code inside a
- * framework whose memory pool owns the device and forbids allocations it
- * does not track, or a time-critical loop that cannot pay for the implicit
- * synchronisation of cudaMalloc/cudaFree.  It computes exactly what
- * gg_diagnostics_eps computes, from fields the caller already holds:
+ * inside a framework whose memory pool owns the device and forbids
+ * allocations it does not track, or a time-critical loop that cannot pay for
+ * the implicit device-wide synchronisation of cudaMalloc/cudaFree.  It runs
+ * the same reduction kernels as gg_diagnostics_eps, on fields the caller
+ * already holds:
  *   u, v, w: device, ny rows of `pitch` elements (float, or double when
- *     fp64 != 0), row j starting at element j*pitch, nx <= pitch values used;
+ *     fp64 != 0), row j starting at element j*pitch, the first nx used (the
+ *     padding columns are never read);
  *   dx, dy > 0: cell sizes; eps > 0: gap threshold; *out: host result.
  * Its scratch (608 partial records + 1 result record of 16 doubles, 77,952
  * bytes) is a fixed array in the library's device memory, present on every
  * device that loads the library until the process exits.  Limits: nx, ny >= 1,
  * pitch >= nx and nx*ny <= 2^31 cells; anything else returns GG_ERR_ARG
  * before any device work.  The first call on a device looks up the device
- * address of the scratch array (one cudaGetSymbolAddress, no allocation);
- * make that first call before any stream capture on that device.  All calls
- * share the one array, and every record a call reads is written by that same
- * call, so nothing needs clearing between calls; calls whose work overlaps on
- * the GPU (other streams, other host threads) race on the array and must be
- * serialised by the caller.  Returns GG_OK, GG_ERR_NONFINITE (with *out
- * filled), GG_ERR_ARG or GG_ERR_CUDA.  Synchronizes cuda_stream. */
+ * address of the scratch array (one cudaGetSymbolAddress, no allocation).
+ * All calls share the one array, and every record a call reads is written by
+ * that same call, so nothing needs clearing between calls; calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on the array
+ * and must be serialised by the caller.  The result is copied to the host
+ * and cuda_stream is synchronized before the call returns.  Returns GG_OK,
+ * GG_ERR_NONFINITE (with *out filled), GG_ERR_ARG or GG_ERR_CUDA (a failed
+ * launch or copy of this call; an error left pending by an earlier call is
+ * neither reported nor cleared). */
 int gg_diagnostics_noalloc(const void* u, const void* v, const void* w, int32_t fp64,
                            int32_t nx, int32_t ny, int32_t pitch, double dx, double dy,
                            double eps, void* cuda_stream, gg_diag* out);
@@ -263,23 +280,33 @@ int gg_diagnostics_noalloc(const void* u, const void* v, const void* w, int32_t 
  * state it advanced (every plan computes the same bits).  gg_create runs it
  * by itself, once per (nx, ny, precision) and process, when
  * steps_per_pass == 0 and nx*ny >= 2^18.  chosen (may be NULL) receives
- * {T, kernel kind (1 warp, 0 shared memory), strip width, chunk height}.
+ * {T, kernel kind (as gg_plan_info), strip width, chunk height}; the
+ * candidates also include the paired-column warp wavefront (kind 3) with
+ * T = 1..4 and the same chunk heights.
  * A no-op for GG_FP64_PLAIN.  Synchronizes. */
 int gg_autotune(gg_sim* sim, int64_t trial_steps, int32_t* chosen);
 
 /* Choose the launch plan of the FP32 step explicitly: kind 1 = warp-register
- * wavefront (T = 1..4), kind 0 = shared-memory wavefront (T = 1..8);
- * strip = output columns per CTA strip (kind 0 only, 0 = default), chunk =
- * rows per chunk (0 = default).  Every plan computes the same bits.
+ * wavefront (one column per lane, T = 1..4), kind 3 = paired-column warp
+ * wavefront (two columns per lane, 64-column strips, T = 1..4), kind 0 =
+ * shared-memory wavefront (T = 1..8); strip = output columns per CTA strip
+ * (kind 0 only, 0 = default), chunk = rows per chunk (0 = default).  Every
+ * plan computes the same bits.
  * GG_ERR_ARG for values out of range, GG_ERR_STATE for GG_FP64_PLAIN. */
 int gg_set_plan(gg_sim* sim, int32_t kind, int32_t T, int32_t strip, int32_t chunk);
 
 /* Launch plan in use: info[0..3] = kernel (1 warp-register wavefront,
- * 0 shared-memory wavefront, 2 plain FP64), steps per pass T, strip width,
- * chunk height. */
+ * 3 paired-column warp wavefront, 0 shared-memory wavefront, 2 plain FP64),
+ * steps per pass T, strip width (written columns), chunk height. */
 int gg_plan_info(const gg_sim* sim, int32_t* info);
 
-double gg_dt(const gg_sim* sim);              /* fixed dt (0 if sim is NULL) */
+double gg_dt(const gg_sim* sim);              /* dt of the next step (0 if sim is NULL);
+                                                 with the adaptive step it is read from
+                                                 the device (synchronizes) */
+double gg_time(const gg_sim* sim);            /* simulated time advanced since gg_create:
+                                                 steps * dt, or with the adaptive step the
+                                                 sum of the Delta t_k taken (synchronizes);
+                                                 0 if sim is NULL */
 double gg_dt_max(const gg_sim* sim);          /* stable bound dt_max */
 int64_t gg_step_count(const gg_sim* sim);     /* steps taken so far */
 int32_t gg_steps_per_pass(const gg_sim* sim); /* temporal blocking depth in use */
@@ -359,6 +386,18 @@ int gg_batch_launch_info(const gg_batch* b, int32_t* info);
 double gg_batch_dt(const gg_batch* b, int32_t inst);
 const char* gg_batch_last_error(const gg_batch* b);
 int gg_batch_destroy(gg_batch* b);
+
+/* Arithmetic-rate probe (no counterpart in the paper: it measures the
+ * denominators of the ALU rooflines the kernels are reported against).
+ * kind 0: FP64 fused multiply-add, 1: FP32 fused multiply-add, 2: packed
+ * FP32 pairs (two FMAs per instruction).  Launches `waves` whole waves of
+ * 256-thread CTAs (the SM count times the CTAs an SM holds), each thread
+ * running 8 independent FMA chains for `iters` iterations, once to warm up
+ * and once timed with CUDA events on cuda_stream; *flops_per_s = 2 flops per
+ * FMA over the timed launch.  Limits: 1 <= iters <= 2^32, 1 <= waves <= 64;
+ * GG_ERR_ARG outside them or for a NULL result, GG_ERR_CUDA on a failed
+ * launch or query.  Allocates nothing; synchronizes cuda_stream. */
+int gg_probe_fma_rate(int32_t kind, int64_t iters, int32_t waves, void* cuda_stream, double* flops_per_s);
 
 #ifdef __cplusplus
 }

@@ -86,6 +86,10 @@ def _configure(lib):
         lib.ggo_step.restype = None
         lib.ggo_run.argtypes = [P, _D, _D, _D, _D, _D, _D, i64]
         lib.ggo_run.restype = ctypes.c_int
+        lib.ggo_adaptive_dt.argtypes = [P, dbl, dbl, _D, _D, _D]
+        lib.ggo_adaptive_dt.restype = dbl
+        lib.ggo_run_adaptive.argtypes = [P, _D, _D, _D, dbl, dbl, i64, _D, _D, _D, i64, _D, _D]
+        lib.ggo_run_adaptive.restype = ctypes.c_int
         lib.ggo_diagnostics.argtypes = [i32, i32, dbl, dbl, _D, _D, _D, dbl, _D]
         lib.ggo_diagnostics.restype = None
         lib.ggo_step_vjp.argtypes = [P, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]
@@ -213,6 +217,27 @@ def run(s: Setup, a11, a12, a22, U, V, W, nsteps: int):
     if rc != 0:
         raise MemoryError("oracle run: allocation failed")
     return U, V, W
+
+
+def adaptive_dt(s: Setup, lambda_a: float, cfl: float, U, V, W) -> float:
+    """Delta t_k of the adaptive step rule on the state (U, V, W)."""
+    U, V, W = _f64(U), _f64(V), _f64(W)
+    st = s.struct()
+    return float(_load().ggo_adaptive_dt(ctypes.byref(st), float(lambda_a), float(cfl), _p(U), _p(V), _p(W)))
+
+
+def run_adaptive(s: Setup, a11, a12, a22, lambda_a: float, cfl: float, every: int, U, V, W, nsteps: int):
+    """nsteps steps with Delta t_k recomputed every `every` steps; returns
+    (U, V, W), the time advanced and the last Delta t_k."""
+    a11, a12, a22 = _f64(a11), _f64(a12), _f64(a22)
+    U, V, W = (np.array(x, dtype=np.float64, order="C") for x in (U, V, W))
+    st = s.struct()
+    t, dt = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = _load().ggo_run_adaptive(ctypes.byref(st), _p(a11), _p(a12), _p(a22), float(lambda_a), float(cfl),
+                                  int(every), _p(U), _p(V), _p(W), int(nsteps), ctypes.byref(t), ctypes.byref(dt))
+    if rc != 0:
+        raise MemoryError("oracle run: allocation failed")
+    return (U, V, W), t.value, dt.value
 
 
 def diagnostics(U, V, W, dx, dy, eps=0.01):

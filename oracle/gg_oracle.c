@@ -246,6 +246,79 @@ int ggo_run(const ggo_problem* p, const double* a11, const double* a12, const do
     return 0;
 }
 
+/* ------------------------------------------------------------ adaptive Delta t_k */
+
+/* The step of Section 2 recomputed from the state, Delta t_k.  The paper
+ * recomputes Delta t_k after each iteration "to ensure numerical stability"
+ * and gives no formula.  Reading: Delta t_k is the largest step for which the
+ * coefficient of each unknown's own old value in eq. (3) stays at least
+ * 1 - cfl, evaluated on the current state X^k:
+ *   U' = U (1 + dt (1 - U - d W))                      -> kU = U + d W - 1
+ *   V' = V (1 + dt (r (1 - V) - alpha S)) + (neighbours),
+ *        S = sum over the interior faces f of (1 - (U_P + U_nb)/2) / h_f^2
+ *                                                      -> kV = alpha S - r (1 - V)
+ *   W: the acid operator's stable bound, static since A is:
+ *        kW = c + 2 Lambda_A (1/dx^2 + 1/dy^2), Lambda_A = max lambda_max(A)
+ *   Delta t_k = cfl / max(kW, max_cells kU, max_cells kV).
+ * Without reactions the reaction parts (1, d, r, c) are left out.  For
+ * states in [0, 1] it is never below the fixed step of ggo_dt_max. */
+double ggo_adaptive_dt(const ggo_problem* p, double Lambda_A, double cfl, const double* U, const double* V,
+                       const double* W)
+{
+    int nx = p->nx, ny = p->ny;
+    double hx2 = p->dx * p->dx, hy2 = p->dy * p->dy;
+    double kW = 2.0 * Lambda_A * (1.0 / hx2 + 1.0 / hy2) + (p->no_reaction ? 0.0 : p->c);
+    double kU = 0.0, kV = 0.0;
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            double u = AT(U, i, j), v = AT(V, i, j), w = AT(W, i, j);
+            double S = 0.0;
+            if (i + 1 < nx) S += (1.0 - 0.5 * (u + AT(U, i + 1, j))) / hx2;
+            if (i - 1 >= 0) S += (1.0 - 0.5 * (u + AT(U, i - 1, j))) / hx2;
+            if (j + 1 < ny) S += (1.0 - 0.5 * (u + AT(U, i, j + 1))) / hy2;
+            if (j - 1 >= 0) S += (1.0 - 0.5 * (u + AT(U, i, j - 1))) / hy2;
+            double ku = p->no_reaction ? 0.0 : u + p->delta * w - 1.0;
+            double kv = p->D * S - (p->no_reaction ? 0.0 : p->rho * (1.0 - v));
+            if (ku > kU) kU = ku;
+            if (kv > kV) kV = kv;
+        }
+    }
+    double k = kW;
+    if (kU > k) k = kU;
+    if (kV > k) k = kV;
+    return cfl / k;
+}
+
+/* nsteps steps in place with the adaptive step: Delta t_k is recomputed
+ * (ggo_adaptive_dt) at every step k = 0, every, 2 every, ... of this call and
+ * held in between.  *t_out (may be NULL) receives the time advanced,
+ * sum_k Delta t_k, and *dt_out (may be NULL) the last Delta t_k.  p->dt is not
+ * used.  Returns 0, or -1 if scratch memory could not be allocated. */
+int ggo_run_adaptive(const ggo_problem* p, const double* a11, const double* a12, const double* a22,
+                     double Lambda_A, double cfl, int64_t every, double* U, double* V, double* W, int64_t nsteps,
+                     double* t_out, double* dt_out)
+{
+    size_t n = (size_t)p->nx * (size_t)p->ny;
+    double* buf = (double*)malloc(3 * n * sizeof(double));
+    if (!buf) return -1;
+    double *u2 = buf, *v2 = buf + n, *w2 = buf + 2 * n;
+    ggo_problem q = *p;
+    double t = 0.0;
+    if (every < 1) every = 1;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        if (k % every == 0) q.dt = ggo_adaptive_dt(p, Lambda_A, cfl, U, V, W);
+        ggo_step(&q, a11, a12, a22, U, V, W, u2, v2, w2);
+        memcpy(U, u2, n * sizeof(double));
+        memcpy(V, v2, n * sizeof(double));
+        memcpy(W, w2, n * sizeof(double));
+        t += q.dt;
+    }
+    if (t_out) *t_out = t;
+    if (dt_out) *dt_out = q.dt;
+    free(buf);
+    return 0;
+}
+
 /* ------------------------------------------------------------ diagnostics */
 
 /* out[0..2]  integrals dx dy sum F of U, V, W

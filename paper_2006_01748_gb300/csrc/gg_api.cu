@@ -41,6 +41,7 @@ double stable_dt_max(double dx, double dy, double Lambda, const gg_params& p)
 Rates32 make_rates32(double dx, double dy, double dt, const gg_params& p)
 {
     Rates32 r;
+    r.dt_dev = nullptr;
     r.dt = (float)dt;
     r.D = (float)p.D;
     r.delta = (float)p.delta;
@@ -61,7 +62,32 @@ Rates32 make_rates32(double dx, double dy, double dt, const gg_params& p)
     return r;
 }
 
-Rates32 rates32(const gg_sim* s) { return make_rates32(s->dx, s->dy, s->dt, s->params); }
+Rates32 rates32(const gg_sim* s)
+{
+    Rates32 r = make_rates32(s->dx, s->dy, s->dt, s->params);
+    if (s->params.adapt_every > 0) r.dt_dev = s->adapt.dt32;
+    return r;
+}
+
+cudaError_t adapt_now(gg_sim* s)
+{
+    const bool fp64 = s->params.precision == GG_FP64_PLAIN;
+    const int nr = (s->params.flags & GG_FLAG_NO_REACTION) ? 1 : 0;
+    const double ihx2 = 1.0 / (s->dx * s->dx), ihy2 = 1.0 / (s->dy * s->dy);
+    cudaError_t e;
+    if (fp64) {
+        AdaptRule<double> r{s->params.D, s->params.rho, s->params.delta, ihx2, ihy2, nr};
+        e = launch_adapt<double>(s->f64[s->cur][0], s->f64[s->cur][1], s->f64[s->cur][2], s->nx, s->ny, s->pitch, r,
+                                 s->kW, s->params.cfl, s->since_adapt, s->adapt, s->stream);
+    } else {
+        AdaptRule<float> r{(float)s->params.D, (float)s->params.rho, (float)s->params.delta, (float)ihx2,
+                           (float)ihy2, nr};
+        e = launch_adapt<float>(s->f32[s->cur][0], s->f32[s->cur][1], s->f32[s->cur][2], s->nx, s->ny, s->pitch, r,
+                                s->kW, s->params.cfl, s->since_adapt, s->adapt, s->stream);
+    }
+    if (e == cudaSuccess) s->since_adapt = 0;
+    return e;
+}
 
 Grid32 grid32(const gg_sim* s, int cur)
 {
@@ -89,9 +115,23 @@ Plan32 default_plan(int nx, int ny, int T)
     p.halo = T;
     p.threads = 128;
     if (T <= 4) {
-        // warp-register wavefront; chunk heights from the 8192 x 8192 sweep
-        // (64 rows for T <= 2, 128 for T = 3, 256 for T = 4), lowered when the
-        // grid would give fewer than about 16 warps per SM
+        // warp-register wavefront, two columns per lane for T >= 2 (the
+        // faster kernel at every T >= 2 on the 8192 x 8192 tissue); chunk
+        // heights from the 8192 x 8192 sweeps (64 rows for T <= 2, 128 for
+        // T = 3 and for the paired T = 4, 256 for the one-column T = 4),
+        // lowered when the grid would give fewer than about 16 warps per SM
+        if (T >= 2) {
+            p.kind = 3;
+            const int out = stepw2_out_columns(T);
+            const int nstrips = (nx + out - 1) / out;
+            const int preferred = T <= 2 ? 64 : 128;
+            const int chunks = std::max(1, (12 * 152 + nstrips - 1) / nstrips);
+            int H = round_up((ny + chunks - 1) / chunks, 8);
+            H = std::max(std::min(H, preferred), 4 * T + 8);
+            p.by = std::min(ny, H);
+            p.bx = out;
+            return p;
+        }
         p.kind = 1;
         const int out = 32 - 2 * T;
         const int nstrips = (nx + out - 1) / out;
@@ -166,6 +206,30 @@ Plan32 tune_plan(gg_sim* s, int64_t trial_steps)
             if (H < 4 * T + 8 && H != 256) continue;
             Plan32 p = default_plan(s->nx, s->ny, T);
             p.kind = 1;
+            p.bx = 32 - 2 * T;
+            p.by = std::min(s->ny, H);
+            cands.push_back(p);
+        }
+        // the paired-column warp wavefront: fixed heights and the whole-wave ones
+        std::vector<int> H2 = {16, 32, 64, 128, 256};
+        const int wave2 = stepw2_wave_warps(T, kahan);
+        const int strips2 = (s->nx + stepw2_out_columns(T) - 1) / stepw2_out_columns(T);
+        if (wave2 > 0 && strips2 <= wave2) {
+            int added = 0;
+            for (int m = 1; added < 4; ++m) {
+                const int nch = m * (wave2 / strips2);
+                const int H = (s->ny + nch - 1) / nch;
+                if (H < 4 * T + 8) break;
+                if (H > 256) continue;
+                if (std::find(H2.begin(), H2.end(), H) == H2.end()) H2.push_back(H);
+                ++added;
+            }
+        }
+        for (int H : H2) {
+            if (H < 4 * T + 8 && H != 256) continue;
+            Plan32 p = default_plan(s->nx, s->ny, T);
+            p.kind = 3;
+            p.bx = stepw2_out_columns(T);
             p.by = std::min(s->ny, H);
             cands.push_back(p);
         }
@@ -267,7 +331,8 @@ int validate(const gg_grid* grid, const gg_params* params, std::string& why)
     }
     if (p.flags & ~(GG_FLAG_NO_REACTION | GG_FLAG_ALLOW_UNSTABLE)) { why = "unknown flag bits"; return GG_ERR_ARG; }
     if (p.steps_per_pass < 0 || p.steps_per_pass > kMaxT) { why = "steps_per_pass must lie in [0, 8]"; return GG_ERR_ARG; }
-    if (p.reserved != 0) { why = "reserved must be 0"; return GG_ERR_ARG; }
+    if (p.adapt_every < 0) { why = "adapt_every must be >= 0"; return GG_ERR_ARG; }
+    if (p.adapt_every > 0 && p.dt != 0.0) { why = "an explicit dt and the adaptive step exclude each other"; return GG_ERR_ARG; }
     return GG_OK;
 }
 
@@ -330,7 +395,7 @@ int gg_create(const gg_grid* grid, const gg_params* params, const double* theta,
     const size_t fstride = (fbytes + 255) / 256 * 256;
     const int nstate = kahan ? 6 : 3;
     const size_t dense_stride = (n * 8 + 255) / 256 * 256;
-    const size_t diag_bytes = (size_t)kDiagBlocks * kDiagStride * 8 + 32 * 8;
+    const size_t diag_bytes = (size_t)kDiagBlocks * kDiagStride * 8 + 40 * 8;
     // arena: 2 x nstate state fields, 3 tensor fields, theta/l1/l2 (FP64 dense), diagnostics
     const size_t keep_tensor = fp64 ? 0 : 3;
     const size_t arena = fstride * (2 * nstate + 3) + dense_stride * keep_tensor + diag_bytes + 256;
@@ -360,6 +425,11 @@ int gg_create(const gg_grid* grid, const gg_params* params, const double* theta,
     p += (size_t)kDiagBlocks * kDiagStride * 8;
     s->diag_out = (double*)p;            // 16 doubles
     s->counters = (unsigned long long*)(s->diag_out + 16);  // [0] bad lambda, [1] nonfinite, [2] lmax bits
+    // adaptive step words: Delta t_k (FP64), simulated time, Delta t_k (FP32), two maxima
+    s->adapt.dt64 = s->diag_out + 32;
+    s->adapt.t_done = s->diag_out + 33;
+    s->adapt.dt32 = (float*)(s->diag_out + 34);
+    s->adapt.kmax = (void*)(s->diag_out + 36);
     // Zero the whole arena once: padding columns and compensation terms start at 0.
     e = cudaMemsetAsync(s->arena, 0, arena, s->stream);
     if (e != cudaSuccess) { rc = cuda_fail(s, e, "memset"); g_create_error = s->last_error; gg_destroy(s); return rc; }
@@ -416,7 +486,16 @@ int gg_create(const gg_grid* grid, const gg_params* params, const double* theta,
     memcpy(&lmax, &cnt[2], sizeof lmax);
     s->lambda_max = lmax;
     s->dt_max = stable_dt_max(s->dx, s->dy, lmax, s->params);
-    if (s->params.dt > 0.0) {
+    if (s->params.adapt_every > 0) {
+        // acid part of the rule; Delta t_0 from the initial state
+        s->kW = 2.0 * lmax * (1.0 / (s->dx * s->dx) + 1.0 / (s->dy * s->dy)) +
+                ((s->params.flags & GG_FLAG_NO_REACTION) ? 0.0 : s->params.c);
+        s->since_adapt = 0;
+        e = adapt_now(s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&s->dt, s->adapt.dt64, 8, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) { rc = cuda_fail(s, e, "adaptive step"); g_create_error = s->last_error; gg_destroy(s); return rc; }
+    } else if (s->params.dt > 0.0) {
         if (s->params.dt > s->dt_max && !(s->params.flags & GG_FLAG_ALLOW_UNSTABLE)) {
             char b[160];
             snprintf(b, sizeof b, "dt = %.6g exceeds the stable bound %.6g", s->params.dt, s->dt_max);
@@ -442,13 +521,14 @@ int gg_create(const gg_grid* grid, const gg_params* params, const double* theta,
     return GG_OK;
 }
 
-int gg_step(gg_sim* s, int64_t nsteps)
+// Steps of the fixed-step path; with the adaptive step gg_step calls it for
+// the stretches between recomputations of Delta t_k.
+static cudaError_t run_steps(gg_sim* s, int64_t nsteps)
 {
-    if (!s) return GG_ERR_ARG;
-    if (nsteps < 0) { s->last_error = "nsteps < 0"; return GG_ERR_ARG; }
     cudaError_t e = cudaSuccess;
     if (s->params.precision == GG_FP64_PLAIN) {
         Rates64 r;
+        r.dt_dev = s->params.adapt_every > 0 ? s->adapt.dt64 : nullptr;
         r.dt = s->dt; r.D = s->params.D; r.delta = s->params.delta; r.rho = s->params.rho; r.c = s->params.c;
         r.kx = 0.5 / (s->dx * s->dx); r.ky = 0.5 / (s->dy * s->dy); r.kc = 0.25 / (s->dx * s->dy);
         r.ihx2 = 1.0 / (s->dx * s->dx); r.ihy2 = 1.0 / (s->dy * s->dy);
@@ -473,11 +553,58 @@ int gg_step(gg_sim* s, int64_t nsteps)
             if (e == cudaSuccess) { s->cur ^= 1; s->steps += T; left -= T; }
         }
     }
+    return e;
+}
+
+int gg_step(gg_sim* s, int64_t nsteps)
+{
+    if (!s) return GG_ERR_ARG;
+    if (nsteps < 0) { s->last_error = "nsteps < 0"; return GG_ERR_ARG; }
+    cudaError_t e = cudaSuccess;
+    if (s->params.adapt_every > 0) {
+        // passes never straddle a recomputation of Delta t_k, so every plan
+        // takes the same steps with the same Delta t_k
+        const int64_t every = s->params.adapt_every;
+        int64_t left = nsteps;
+        while (left > 0 && e == cudaSuccess) {
+            if (s->since_adapt == every) e = adapt_now(s);
+            if (e != cudaSuccess) break;
+            const int64_t n = std::min<int64_t>(left, every - s->since_adapt);
+            e = run_steps(s, n);
+            if (e == cudaSuccess) { s->since_adapt += n; left -= n; }
+        }
+    } else {
+        e = run_steps(s, nsteps);
+    }
     if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
     return GG_OK;
 }
 
-double gg_dt(const gg_sim* s) { return s ? s->dt : 0.0; }
+double gg_dt(const gg_sim* s)
+{
+    if (!s) return 0.0;
+    if (s->params.adapt_every <= 0) return s->dt;
+    double dt = 0.0;
+    if (cudaMemcpyAsync(&dt, s->adapt.dt64, 8, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.0;
+    }
+    return dt;
+}
+
+double gg_time(const gg_sim* s)
+{
+    if (!s) return 0.0;
+    if (s->params.adapt_every <= 0) return (double)s->steps * s->dt;
+    double w[2] = {0.0, 0.0};  // Delta t_k, time up to its recomputation
+    if (cudaMemcpyAsync(w, s->adapt.dt64, 16, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.0;
+    }
+    return w[1] + w[0] * (double)s->since_adapt;
+}
 double gg_dt_max(const gg_sim* s) { return s ? s->dt_max : 0.0; }
 int64_t gg_step_count(const gg_sim* s) { return s ? s->steps : 0; }
 int32_t gg_steps_per_pass(const gg_sim* s) { return s ? (s->params.precision == GG_FP64_PLAIN ? 1 : s->plan.T) : 0; }
@@ -625,10 +752,10 @@ int gg_set_plan(gg_sim* s, int32_t kind, int32_t T, int32_t strip, int32_t chunk
 {
     if (!s) return GG_ERR_ARG;
     if (s->params.precision == GG_FP64_PLAIN) { s->last_error = "FP64 has a single plan"; return GG_ERR_STATE; }
-    if (kind != 0 && kind != 1) { s->last_error = "kind must be 0 or 1"; return GG_ERR_ARG; }
-    if (T < 1 || T > (kind == 1 ? 4 : kMaxT)) { s->last_error = "T out of range for this kernel"; return GG_ERR_ARG; }
+    if (kind != 0 && kind != 1 && kind != 3) { s->last_error = "kind must be 0, 1 or 3"; return GG_ERR_ARG; }
+    if (T < 1 || T > (kind != 0 ? 4 : kMaxT)) { s->last_error = "T out of range for this kernel"; return GG_ERR_ARG; }
     if (chunk < 0 || strip < 0 || chunk > (1 << 20) || strip > 1024) { s->last_error = "bad strip or chunk"; return GG_ERR_ARG; }
-    Plan32 p = default_plan(s->nx, s->ny, kind == 1 ? T : kMaxT);
+    Plan32 p = default_plan(s->nx, s->ny, kind != 0 ? T : kMaxT);
     p.kind = kind;
     p.T = T;
     p.halo = T;
@@ -638,7 +765,9 @@ int gg_set_plan(gg_sim* s, int32_t kind, int32_t T, int32_t strip, int32_t chunk
         if ((sw + p.threads - 1) / p.threads > 3) { s->last_error = "strip too wide"; return GG_ERR_ARG; }
     }
     if (chunk > 0) p.by = std::min(s->ny, chunk);
-    if (kind == 1 && chunk == 0) p.by = default_plan(s->nx, s->ny, T).by;
+    if (kind != 0 && chunk == 0) p.by = default_plan(s->nx, s->ny, T).by;
+    if (kind == 3) p.bx = stepw2_out_columns(T);
+    if (kind == 1) p.bx = 32 - 2 * T;
     s->plan = p;
     return GG_OK;
 }

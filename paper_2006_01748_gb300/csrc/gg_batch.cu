@@ -399,6 +399,7 @@ int gg_batch_create(int32_t n, const gg_grid* grids, const gg_params* params, co
     if (prec != GG_FP32 && prec != GG_FP32_KAHAN) return GG_ERR_ARG;
     for (int k = 0; k < n; ++k) {
         if (params[k].precision != prec) return GG_ERR_ARG;
+        if (params[k].adapt_every != 0) return GG_ERR_ARG;  // ensembles run fixed steps
         for (int m = 0; m < 6; ++m)
             if (!fields[6 * k + m]) return GG_ERR_ARG;
         if (params[k].steps_per_pass > kBatchMaxT || params[k].steps_per_pass != params[0].steps_per_pass)

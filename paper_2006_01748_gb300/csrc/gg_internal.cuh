@@ -33,8 +33,12 @@ struct Grid32 {
     int nx, ny, pitch;
 };
 
-// Scalars of eq. (3) in FP32, rounded once from the FP64 host values.
+// Scalars of eq. (3) in FP32, rounded once from the FP64 host values.  With
+// the adaptive step, dt_dev points at the device copy of the current
+// Delta t_k and the kernels read dt there (dt itself is then unused); with the
+// fixed step it is null.
 struct Rates32 {
+    const float* dt_dev;
     float dt, D, delta, rho, c;
     float kx, ky, kc;     // 0.5/dx^2, 0.5/dy^2, 0.25/(dx dy)
     float ihx2, ihy2;     // 1/dx^2, 1/dy^2
@@ -48,7 +52,9 @@ Rates32 make_rates32(double dx, double dy, double dt, const gg_params& p);
 // Launch plan of the FP32 step.  kind 0: shared-memory wavefront (strips of
 // bx output columns plus a halo of `halo` columns on each side, chunks of by
 // output rows, `threads` threads per CTA); kind 1: warp-register wavefront
-// (strips of 32 - 2T columns per warp, chunks of by rows).  T steps per pass.
+// (strips of 32 - 2T columns per warp, chunks of by rows); kind 3: the
+// paired-column warp wavefront (strips of 64 columns, 60 or 56 of them
+// written, chunks of by rows).  T steps per pass.
 struct Plan32 {
     int kind = 1;
     int T = 1;
@@ -71,6 +77,14 @@ struct Stash32 {
 };
 cudaError_t launch_stepw_stash(const Grid32& g, const Rates32& r, int H, int T, bool kahan, const Stash32& st,
                                cudaStream_t s);
+// Paired-column warp wavefront (two columns per lane, 64-column strips):
+// the same interface as launch_stepw / launch_stepw_stash / stepw_wave_warps,
+// and the columns a strip writes for T steps per pass.
+cudaError_t launch_stepw2(const Grid32& g, const Rates32& r, int H, int T, bool kahan, cudaStream_t s);
+cudaError_t launch_stepw2_stash(const Grid32& g, const Rates32& r, int H, int T, bool kahan, const Stash32& st,
+                                cudaStream_t s);
+int stepw2_wave_warps(int T, bool kahan);
+int stepw2_out_columns(int T);
 // One pass of T steps with the kernel the plan names.
 cudaError_t launch_plan(const Grid32& g, const Rates32& r, const Plan32& p, int T, bool kahan, cudaStream_t s);
 cudaError_t launch_step32(const Grid32& g, const Rates32& r, const Plan32& p, int T, bool kahan,
@@ -84,6 +98,7 @@ struct Grid64 {
     int nx, ny, pitch;
 };
 struct Rates64 {
+    const double* dt_dev;  // as Rates32::dt_dev
     double dt, D, delta, rho, c;
     double kx, ky, kc, ihx2, ihy2;
     int no_reaction;
@@ -118,6 +133,38 @@ cudaError_t launch_pack(const void* src, bool src_fp64, void* dst, bool dst_fp64
 // [10] tumour cells, [11] gap cells (scaled by dx dy on the host).
 cudaError_t launch_diagnostics(const void* u, const void* v, const void* w, bool fp64, int nx, int ny,
                                int pitch, double eps, double* partials, double* out, cudaStream_t s);
+
+// The rates a kernel runs with: dt from the device when the step is adaptive.
+__device__ __forceinline__ Rates32 live_rates(const Rates32& k)
+{
+    Rates32 r = k;
+    if (k.dt_dev) r.dt = __ldg(k.dt_dev);
+    return r;
+}
+__device__ __forceinline__ Rates64 live_rates(const Rates64& k)
+{
+    Rates64 r = k;
+    if (k.dt_dev) r.dt = __ldg(k.dt_dev);
+    return r;
+}
+
+// Adaptive step Delta t_k (gg_adapt.cu): per-cell terms of the rule in the
+// state's precision F, and the device words it keeps.
+template <typename F> struct AdaptRule {
+    F D, rho, delta, ihx2, ihy2;
+    int no_reaction;
+};
+struct AdaptState {
+    double* dt64;     // current Delta t_k
+    float* dt32;      // the same, rounded once, for the FP32 kernels
+    double* t_done;   // simulated time up to the last recomputation
+    void* kmax;       // two maxima (kU, kV) as bit patterns, zero between reductions
+};
+// Reduces the state's maxima, then sets Delta t_k = cfl / max(kW, kU, kV) and
+// adds steps_prev times the previous Delta t to the simulated time.
+template <typename F>
+cudaError_t launch_adapt(const F* u, const F* v, const F* w, int nx, int ny, int pitch, const AdaptRule<F>& r,
+                         double kW, double cfl, long long steps_prev, AdaptState& st, cudaStream_t s);
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 

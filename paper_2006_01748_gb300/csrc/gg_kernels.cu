@@ -15,8 +15,9 @@ namespace {
 // One thread per cell, every operand read from global memory: the plain
 // design (the CUDA kernel of Section 3 updates each cell from the previous
 // iterate in global memory), kept as the double-precision comparison point.
-__global__ void __launch_bounds__(256) step64_kernel(const Grid64 g, const Rates64 k)
+__global__ void __launch_bounds__(256) step64_kernel(const Grid64 g, const Rates64 k0)
 {
+    const Rates64 k = live_rates(k0);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int nx = g.nx, ny = g.ny, pitch = g.pitch;
@@ -379,18 +380,20 @@ cudaError_t launch_pack(const void* src, bool src_fp64, void* dst, bool dst_fp64
     return cudaGetLastError();
 }
 
+// Each launch's own status is checked (cudaLaunchKernel returns it), so an
+// error left pending on the calling thread by some earlier call is neither
+// reported as this reduction's failure nor cleared.
 cudaError_t launch_diagnostics(const void* u, const void* v, const void* w, bool fp64, int nx, int ny, int pitch,
                                double eps, double* partials, double* out, cudaStream_t s)
 {
-    const int blocks = std::min(ny, kDiagBlocks);
-    if (fp64)
-        diag_partial_kernel<double><<<blocks, 256, 0, s>>>((const double*)u, (const double*)v, (const double*)w, nx,
-                                                           ny, pitch, eps, partials);
-    else
-        diag_partial_kernel<float><<<blocks, 256, 0, s>>>((const float*)u, (const float*)v, (const float*)w, nx, ny,
-                                                          pitch, eps, partials);
-    diag_final_kernel<<<1, 256, 0, s>>>(partials, blocks, out);
-    return cudaGetLastError();
+    int blocks = std::min(ny, kDiagBlocks);
+    void* pargs[] = {(void*)&u, (void*)&v, (void*)&w, (void*)&nx, (void*)&ny, (void*)&pitch, (void*)&eps,
+                     (void*)&partials};
+    const void* partial = fp64 ? (const void*)diag_partial_kernel<double> : (const void*)diag_partial_kernel<float>;
+    cudaError_t e = cudaLaunchKernel(partial, dim3(blocks), dim3(256), pargs, 0, s);
+    if (e != cudaSuccess) return e;
+    void* fargs[] = {(void*)&partials, (void*)&blocks, (void*)&out};
+    return cudaLaunchKernel((const void*)diag_final_kernel, dim3(1), dim3(256), fargs, 0, s);
 }
 
 }  // namespace gg

@@ -16,6 +16,11 @@ struct gg_sim {
     cudaStream_t stream = nullptr;
     gg::Plan32 plan;
 
+    // adaptive step (params.adapt_every > 0)
+    int64_t since_adapt = 0;         // steps taken since Delta t_k was last recomputed
+    double kW = 0;                   // static acid part of the rule
+    gg::AdaptState adapt{};          // device words, inside the arena
+
     void* arena = nullptr;           // one allocation for state, tensor, diagnostics
     size_t arena_bytes = 0;
     float* f32[2][6] = {};           // [buffer][u, v, w, cu, cv, cw]
@@ -40,6 +45,9 @@ Grid32 grid32(const gg_sim* s, int cur);
 Plan32 default_plan(int nx, int ny, int T);
 double stable_dt_max(double dx, double dy, double Lambda, const gg_params& p);
 Plan32 tune_plan(gg_sim* s, int64_t trial_steps);
+// Recomputes Delta t_k from the current state (adaptive step), adding
+// since_adapt steps of the previous Delta t to the simulated time.
+cudaError_t adapt_now(gg_sim* s);
 }  // namespace gg
 
 // Frees workspaces owned by other translation units (adjoint).

@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256) step32_kernel(const Grid32 g, const Rates
                                                      const int halo, const int sw)
 {
     extern __shared__ float smem[];
-    tile_pass<T, KAHAN, MAXM>(g, k, bx, by, halo, sw, blockIdx.x, blockIdx.y, smem);
+    tile_pass<T, KAHAN, MAXM>(g, live_rates(k), bx, by, halo, sw, blockIdx.x, blockIdx.y, smem);
 }
 
 template <int T, bool KAHAN>

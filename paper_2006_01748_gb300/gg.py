@@ -35,6 +35,12 @@ PRECISIONS = {"fp64": GG_FP64_PLAIN, "fp64_plain": GG_FP64_PLAIN, "fp32": GG_FP3
 FIELDS = {"u": 0, "v": 1, "w": 2, "comp_u": 3, "comp_v": 4, "comp_w": 5, "a11": 6, "a12": 7, "a22": 8,
           "face_x": 9, "face_y": 10, "cross": 11}
 
+# launch-plan kinds of gg_set_plan / gg_plan_info: shared-memory wavefront,
+# warp-register wavefront (one column per lane), the plain FP64 kernel, and
+# the paired-column warp wavefront (two columns per lane)
+PLAN_KINDS = {"smem": 0, "warp": 1, "warp2": 3}
+PLAN_NAMES = {0: "smem", 1: "warp", 2: "fp64", 3: "warp2"}
+
 GG_FLAG_NO_REACTION = 1
 GG_FLAG_ALLOW_UNSTABLE = 2
 
@@ -47,7 +53,7 @@ class gg_params(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("rho", ctypes.c_double), ("D", ctypes.c_double),
                 ("c", ctypes.c_double), ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("steps_per_pass", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("steps_per_pass", ctypes.c_int32), ("adapt_every", ctypes.c_int32)]
 
 
 class gg_diag(ctypes.Structure):
@@ -94,6 +100,7 @@ _SIGNATURES = {
     "gg_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
     "gg_dt": (ctypes.c_double, [_VP]),
     "gg_dt_max": (ctypes.c_double, [_VP]),
+    "gg_time": (ctypes.c_double, [_VP]),
     "gg_step_count": (_I64, [_VP]),
     "gg_steps_per_pass": (_I32, [_VP]),
     "gg_last_error": (ctypes.c_char_p, [_VP]),
@@ -112,6 +119,7 @@ _SIGNATURES = {
     "gg_batch_set_plan": (ctypes.c_int, [_VP, _I32, _I32, _I32]),
     "gg_batch_last_error": (ctypes.c_char_p, [_VP]),
     "gg_batch_destroy": (ctypes.c_int, [_VP]),
+    "gg_probe_fma_rate": (ctypes.c_int, [_I32, _I64, _I32, _VP, _DP]),
 }
 
 
@@ -224,6 +232,13 @@ def gg_destroy(sim):
     return lib().gg_destroy(sim)
 
 
+def gg_probe_fma_rate(kind, iters, waves=4, stream=None):
+    """Measured FMA rate (flop/s) of kind 0 FP64, 1 FP32, 2 packed FP32 pairs."""
+    out = ctypes.c_double(0.0)
+    rc = lib().gg_probe_fma_rate(int(kind), int(iters), int(waves), stream, ctypes.byref(out))
+    return rc, out.value
+
+
 # ---------------------------------------------------------------- helpers
 
 def _f64_host(a, n) -> np.ndarray:
@@ -250,14 +265,14 @@ def _check(rc, sim=None, what="libgg"):
 
 
 def make_params(delta, rho, D, c, precision="fp32_kahan", dt=0.0, cfl=0.9, steps_per_pass=0,
-                no_reaction=False, allow_unstable=False) -> gg_params:
+                no_reaction=False, allow_unstable=False, adapt_every=0) -> gg_params:
     p = gg_params()
     p.delta, p.rho, p.D, p.c = float(delta), float(rho), float(D), float(c)
     p.cfl, p.dt = float(cfl), float(dt)
     p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.flags = (GG_FLAG_NO_REACTION if no_reaction else 0) | (GG_FLAG_ALLOW_UNSTABLE if allow_unstable else 0)
     p.steps_per_pass = int(steps_per_pass)
-    p.reserved = 0
+    p.adapt_every = int(adapt_every)
     return p
 
 
@@ -271,13 +286,14 @@ class GGSim:
 
     def __init__(self, nx, ny, theta, lambda1, lambda2, u0, v0, w0, delta, rho, D, c,
                  precision="fp32_kahan", dt=0.0, cfl=0.9, steps_per_pass=0, no_reaction=False,
-                 allow_unstable=False, lx=1.0, ly=1.0, stream=None):
+                 allow_unstable=False, lx=1.0, ly=1.0, stream=None, adapt_every=0):
         self._sim = None
         n = int(nx) * int(ny)
         self.nx, self.ny = int(nx), int(ny)
         arrs = [_f64_host(a, n) for a in (theta, lambda1, lambda2, u0, v0, w0)]
         grid = gg_grid(self.nx, self.ny, float(lx), float(ly))
-        self.params = make_params(delta, rho, D, c, precision, dt, cfl, steps_per_pass, no_reaction, allow_unstable)
+        self.params = make_params(delta, rho, D, c, precision, dt, cfl, steps_per_pass, no_reaction, allow_unstable,
+                                  adapt_every)
         self.precision = self.params.precision
         self._stream = stream if stream is not None else _current_stream()
         rc, sim = gg_create(grid, self.params, *[a.ctypes.data_as(_VP) for a in arrs], stream=self._stream)
@@ -307,6 +323,11 @@ class GGSim:
         return gg_step_count(self._sim)
 
     @property
+    def time(self) -> float:
+        """Simulated time advanced since creation (sum of the steps taken)."""
+        return lib().gg_time(self._sim)
+
+    @property
     def steps_per_pass(self) -> int:
         return gg_steps_per_pass(self._sim)
 
@@ -316,17 +337,16 @@ class GGSim:
     def plan(self) -> Dict:
         info = (_I32 * 4)()
         _check(lib().gg_plan_info(self._sim, info), self._sim, "gg_plan_info")
-        kind = {0: "smem", 1: "warp", 2: "fp64"}[info[0]]
-        return dict(kind=kind, T=info[1], bx=info[2], by=info[3])
+        return dict(kind=PLAN_NAMES[info[0]], T=info[1], bx=info[2], by=info[3])
 
     def set_plan(self, kind: str = "warp", T: int = 1, strip: int = 0, chunk: int = 0):
-        _check(lib().gg_set_plan(self._sim, 1 if kind == "warp" else 0, int(T), int(strip), int(chunk)),
+        _check(lib().gg_set_plan(self._sim, PLAN_KINDS[kind], int(T), int(strip), int(chunk)),
                self._sim, "gg_set_plan")
 
     def autotune(self, trial_steps: int = 24) -> Dict:
         chosen = (_I32 * 4)()
         _check(lib().gg_autotune(self._sim, int(trial_steps), chosen), self._sim, "gg_autotune")
-        return dict(T=chosen[0], kind="warp" if chosen[1] == 1 else "smem", bx=chosen[2], by=chosen[3])
+        return dict(T=chosen[0], kind=PLAN_NAMES[chosen[1]], bx=chosen[2], by=chosen[3])
 
     def read(self, field: str = "v", fp64: bool = True, out=None):
         """Copy a field; into a new host numpy array, into ``out`` when it is

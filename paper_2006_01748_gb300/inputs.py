@@ -225,6 +225,21 @@ def adjoint_2048(nx: int = 2048, ny: Optional[int] = None, steps: int = 10000, s
                    th, l1, l2, u0, v0, w0, steps, seed=s)
 
 
+def growing_tumour(nx: int = 64, ny: Optional[int] = None, steps: int = 500, seed: int = SEED_PLAIN_128 + 7,
+                   lx: float = 1.0, ly: float = 1.0) -> Problem:
+    """Tumour cells in healthy tissue: U = 1 everywhere, V = 1 on a disk of
+    radius 0.2, W = 0; tumour diffusion D = 0.2 well above the acid's
+    lambda in [0.02, 0.08] (heterogeneous, seeded); delta = 3, rho = 1, c = 5.
+    The tumour flux (mobility 1 - U) starts closed and opens as acid builds
+    up and U falls inside the disk: the workload of the adaptive step."""
+    ny = nx if ny is None else ny
+    th, l1, l2 = heterogeneous_tensor(nx, ny, seed, 0.02, 0.08)
+    u0, v0, w0 = tumour_disk(nx, ny, 0.2, centre=(0.5 * lx, 0.5 * ly), lx=lx, ly=ly)
+    u0 = np.ones((ny, nx))
+    return Problem("growing_tumour", nx, ny, 3.0, 1.0, 0.2, 5.0, th, l1, l2, u0, v0, w0, steps, lx=lx, ly=ly,
+                   seed=seed)
+
+
 ENSEMBLE_SIZES = (128, 256, 512, 1024)
 
 

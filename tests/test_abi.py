@@ -55,7 +55,8 @@ def _create(grid, params, n=4):
 
 @pytest.mark.parametrize("bad", [
     dict(nx=0), dict(ny=-3), dict(delta=-1.0), dict(D=float("nan")), dict(cfl=1.5),
-    dict(precision=7), dict(flags=64), dict(steps_per_pass=9), dict(reserved=1), dict(dt=-1.0),
+    dict(precision=7), dict(flags=64), dict(steps_per_pass=9), dict(adapt_every=-1), dict(dt=-1.0),
+    dict(adapt_every=5, dt=1e-6),
 ])
 def test_host_validation_rejects_bad_arguments(lib, bad):
     grid = gg.gg_grid(bad.get("nx", 2), bad.get("ny", 2), 1.0, 1.0)
@@ -67,8 +68,8 @@ def test_host_validation_rejects_bad_arguments(lib, bad):
         p.flags = bad["flags"]
     if "steps_per_pass" in bad:
         p.steps_per_pass = bad["steps_per_pass"]
-    if "reserved" in bad:
-        p.reserved = bad["reserved"]
+    if "adapt_every" in bad:
+        p.adapt_every = bad["adapt_every"]
     rc, sim = _create(grid, p)
     assert rc == gg.GG_ERR_ARG
     assert not sim.value
@@ -93,3 +94,4 @@ def test_null_handles_are_rejected(lib):
     assert lib.gg_batch_set_plan(None, 0, 1, 0) == gg.GG_ERR_ARG
     assert lib.gg_destroy(None) == gg.GG_OK
     assert lib.gg_dt(None) == 0.0
+    assert lib.gg_time(None) == 0.0

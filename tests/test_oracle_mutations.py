@@ -33,6 +33,13 @@ MUTATIONS = {
     "front ray: west ray walks east": ("else if (d == 1) { L = i0 + 1; di = -1; h = dx; }",
                                        "else if (d == 1) { L = i0 + 1; di = 1; h = dx; }"),
     "front speed without the elapsed time": ("/ (elapsed * (1.0 - 0.0));", "/ (1.0 - 0.0);"),
+    "adaptive step: dx for the north face": ("if (j + 1 < ny) S += (1.0 - 0.5 * (u + AT(U, i, j + 1))) / hy2;",
+                                             "if (j + 1 < ny) S += (1.0 - 0.5 * (u + AT(U, i, j + 1))) / hx2;"),
+    "adaptive step: logistic term with the wrong sign": ("- (p->no_reaction ? 0.0 : p->rho * (1.0 - v));",
+                                                         "+ (p->no_reaction ? 0.0 : p->rho * (1.0 - v));"),
+    "adaptive step: U bound without the acid": ("u + p->delta * w - 1.0;", "u - 1.0;"),
+    "adaptive step: mobility of the own cell only": ("if (i - 1 >= 0) S += (1.0 - 0.5 * (u + AT(U, i - 1, j))) / hx2;",
+                                                     "if (i - 1 >= 0) S += (1.0 - u) / hx2;"),
 }
 
 PIN_TESTS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_")]

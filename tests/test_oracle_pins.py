@@ -67,6 +67,137 @@ def test_dt_rule_keeps_diagonals_nonnegative():
         assert 1 - dt * 4 * max(lam, D) / h ** 2 >= 0      # V centre
 
 
+# --------------------------------------------------------------- adaptive Delta t_k
+
+def _setup(nx, ny, delta=12.5, rho=1.0, D=4e-5, c=70.0, lx=1.0, ly=1.0, no_reaction=False):
+    return oracle.Setup(nx, ny, delta, rho, D, c, 0.0, no_reaction, lx, ly)
+
+
+def test_adaptive_dt_closed_forms():
+    """Uniform and single-cell states where the rule's maxima are known by
+    hand: the V bound with every face of an interior cell at mobility 1, the
+    U bound of healthy tissue with acid, the static acid bound, and a corner
+    cell (two faces) as the only cell with mobility 1/2."""
+    nx, ny, lx, ly = 7, 5, 1.0, 0.6
+    dx, dy = lx / nx, ly / ny
+    lam, cfl = 0.2, 0.9
+    kW = 70.0 + 2 * lam * (1 / dx ** 2 + 1 / dy ** 2)
+    z, one = np.zeros((ny, nx)), np.ones((ny, nx))
+    # U = V = W = 0, D = 3 lam: interior cells have four faces of mobility 1
+    s = _setup(nx, ny, D=3 * lam, lx=lx, ly=ly)
+    kV = 3 * lam * (2 / dx ** 2 + 2 / dy ** 2) - 1.0
+    assert kV > kW
+    assert oracle.adaptive_dt(s, lam, cfl, z, z, z) == pytest.approx(cfl / kV, rel=1e-15)
+    # healthy tissue full of acid (U = V = W = 1): mobility 0, U bound delta
+    s = _setup(nx, ny, delta=1e7, lx=lx, ly=ly)
+    assert oracle.adaptive_dt(s, lam, cfl, one, one, one) == pytest.approx(cfl / 1e7, rel=1e-15)
+    # U = 1, V = W = 0: only the acid bound is positive
+    s = _setup(nx, ny, lx=lx, ly=ly)
+    assert oracle.adaptive_dt(s, lam, cfl, one, z, z) == pytest.approx(cfl / kW, rel=1e-15)
+    # without reactions the acid bound loses c
+    s = _setup(nx, ny, lx=lx, ly=ly, no_reaction=True)
+    assert oracle.adaptive_dt(s, lam, cfl, one, z, z) == pytest.approx(cfl / (kW - 70.0), rel=1e-15)
+    # a tumour corner cell (U = 0) in healthy tissue, V = 1: its two faces
+    # have mobility 1/2, every other face 0 or 1/2 on one side only
+    U = one.copy()
+    U[0, 0] = 0.0
+    s = _setup(nx, ny, D=1e3, lx=lx, ly=ly)
+    expect = 1e3 * 0.5 * (1 / dx ** 2 + 1 / dy ** 2)
+    assert expect > kW
+    assert oracle.adaptive_dt(s, lam, cfl, U, one, z) == pytest.approx(cfl / expect, rel=1e-15)
+
+
+def _own_coefficients(s, a, U, V, W, dt):
+    """d(U', V', W')_P / d(U, V, W)_P of one oracle step, by central
+    differences with the cells perturbed three apart in x and y (so that no
+    perturbed cell sees another in its nine-point stencil); exact for the
+    quadratic step up to rounding."""
+    st = oracle.Setup(s.nx, s.ny, s.delta, s.rho, s.D, s.c, dt, s.no_reaction, s.lx, s.ly)
+    out = [np.zeros_like(U) for _ in range(3)]
+    eps = 1e-4
+    for f in range(3):
+        for oy in range(3):
+            for ox in range(3):
+                m = np.zeros_like(U)
+                m[oy::3, ox::3] = 1.0
+                X = [U.copy(), V.copy(), W.copy()]
+                Xp, Xm = [x.copy() for x in X], [x.copy() for x in X]
+                Xp[f] += eps * m
+                Xm[f] -= eps * m
+                yp = oracle.step(st, *a, *Xp)[f]
+                ym = oracle.step(st, *a, *Xm)[f]
+                out[f] += m * (yp - ym) / (2 * eps)
+    return out
+
+
+def test_adaptive_dt_is_the_largest_step_keeping_own_coefficients():
+    """On states where the logistic factors are frozen (V = 0 for V, U = 0
+    for U), d V'_P / d V_P = 1 - dt kV_P and d U'_P / d U_P = 1 - dt kU_P, so
+    the step's own derivative (the tumour operator of Table 1, not the
+    rule's face sum) shows the rule: with the adaptive dt every such
+    coefficient is >= 1 - cfl, and the binding one equals it."""
+    nx, ny = 9, 7
+    cfl = 0.8
+    th = inputs.white_noise(nx, ny, 31, 0.0, math.pi)
+    l1 = inputs.white_noise(nx, ny, 32, 0.1, 0.3)
+    l2 = inputs.white_noise(nx, ny, 33, 0.05, 0.1)
+    a = oracle.coefficients(th, l1, l2)
+    lam = oracle.lambda_max(*a)
+    z = np.zeros((ny, nx))
+    # V bound binding: large D, rough mobility
+    s = _setup(nx, ny, D=2.0, lx=1.0, ly=0.8)
+    U = inputs.white_noise(nx, ny, 34, 0.0, 1.0)
+    W = inputs.white_noise(nx, ny, 35, 0.0, 1.0)
+    dt = oracle.adaptive_dt(s, lam, cfl, U, z, W)
+    cV = _own_coefficients(s, a, U, z, W, dt)[1]
+    assert cV.min() >= 1 - cfl - 1e-12
+    assert cV.min() == pytest.approx(1 - cfl, abs=1e-9)
+    # U bound binding: huge delta on U = 0 with acid
+    s = _setup(nx, ny, delta=5e3)
+    dt = oracle.adaptive_dt(s, lam, cfl, z, z, W)
+    cU = _own_coefficients(s, a, z, z, W, dt)[0]
+    assert cU.min() >= 1 - cfl - 1e-12
+    assert cU.min() == pytest.approx(1 - cfl, abs=1e-9)
+
+
+def test_adaptive_dt_never_below_the_fixed_step_and_runs():
+    """For states in [0, 1] the adaptive step is at least the fixed step of
+    the static rule; held for a whole run it reproduces the fixed-step run
+    with that dt bit for bit; and on a tissue whose tumour region grows (large
+    D, U -> 0 inside the disk) it shrinks over time while U, V, W stay in
+    [0, 1] (a12 = 0)."""
+    nx, ny = 24, 20
+    p = inputs.plain_128(nx, ny, steps=0)
+    a = oracle.coefficients(p.theta, p.lambda1, p.lambda2)
+    lam = oracle.lambda_max(*a)
+    s = _setup(nx, ny)
+    for seed in range(3):
+        U, V, W = inputs.random_state(nx, ny, 40 + seed)
+        fixed = 0.9 * oracle.dt_max(s.dx, s.dy, lam, s.delta, s.rho, s.D, s.c)
+        assert oracle.adaptive_dt(s, lam, 0.9, U, V, W) >= fixed
+    U0, V0, W0 = inputs.random_state(nx, ny, 44)
+    (Ua, Va, Wa), t, dt = oracle.run_adaptive(s, *a, lam, 0.9, 1000, U0, V0, W0, 30)
+    assert dt == oracle.adaptive_dt(s, lam, 0.9, U0, V0, W0)
+    assert t == pytest.approx(30 * dt, rel=1e-14)
+    sf = oracle.Setup(nx, ny, s.delta, s.rho, s.D, s.c, dt)
+    for x, y in zip((Ua, Va, Wa), oracle.run(sf, *a, U0, V0, W0, 30)):
+        assert np.array_equal(x, y)
+    # isotropic tissue, D = 4 lambda: the V bound takes over as U -> 0
+    th = np.zeros((ny, nx))
+    l = np.full((ny, nx), 0.05)
+    a = oracle.coefficients(th, l, l)
+    s = _setup(nx, ny, delta=3.0, rho=1.0, D=0.2, c=5.0)
+    U0, V0, W0 = inputs.tumour_disk(nx, ny, 0.2)
+    U0 = np.ones((ny, nx))  # healthy tissue with tumour cells: mobility 0 at first
+    dts = []
+    U, V, W = U0, V0, W0
+    for _ in range(20):
+        (U, V, W), t, dt = oracle.run_adaptive(s, *a, 0.05, 0.9, 25, U, V, W, 25)
+        dts.append(dt)
+        assert U.min() >= 0 and U.max() <= 1 and V.min() >= 0 and W.min() >= 0
+    assert dts[-1] < 0.9 * dts[0]
+
+
 # --------------------------------------------------------------- Tables 1, 2
 
 def _read_stencil(name):
