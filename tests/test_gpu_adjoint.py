@@ -224,14 +224,12 @@ def test_adjoint_2048_rate_gradients_against_finite_differences(torch):
     gradients are compared with central differences of the GPU FP64 forward
     (dt held fixed).
 
-    Measured: c 8e-9, rho 5e-7, delta within the rounding floor of the
-    central difference, D 1.5e-3.  The D gradient is held to 2e-3: over this
-    workload's physical time (sqrt(D t) is a third of a cell) a 100 % change
-    of D moves L by about 1e-7 of itself, so its gradient is a sum of
-    per-cell terms lamV D1(V; U) that cancel to a small fraction of their
-    magnitudes, and the FP32 state and sums leave it that accurate.  The same
-    gradient matches the FP64 oracle to 6e-8 on the 128^2 grid over 10^4
-    steps (test_adjoint_10k_steps_matches_oracle)."""
+    The loss is strongly curved in D over this short time (the central
+    difference with h = 1e-3 D is off by 1.5e-3, with h = 3e-2 D it has the
+    wrong sign), so D is differenced with h = 1e-4 D, where the difference
+    has converged to about 1e-5; the other rates with h = 1e-3 of their value.
+    Measured: c 8e-9, rho 5e-7, D 7e-6; delta within the rounding floor of the
+    central difference.  Every gradient is held to 3e-5 plus that floor."""
     p = inputs.adjoint_2048()
     tgt = inputs.adjoint_2048(target=True)
     with gg.GGSim.from_problem(p, precision="fp64") as sim:
@@ -246,15 +244,14 @@ def test_adjoint_2048_rate_gradients_against_finite_differences(torch):
     L0 = _fp64_loss_vw(p, dt, p.steps, Vstar)
     bad = []
     for q, name in ((3, "c"), (2, "D"), (1, "rho"), (0, "delta")):
-        h = 1e-3 * getattr(p, name)
+        h = (1e-4 if name == "D" else 1e-3) * getattr(p, name)
         fd = (_fp64_loss_vw(p, dt, p.steps, Vstar, **{name: getattr(p, name) + h})
               - _fp64_loss_vw(p, dt, p.steps, Vstar, **{name: getattr(p, name) - h})) / (2 * h)
-        noise = 1e-15 * abs(L0) / h   # rounding floor of the central difference
+        noise = 1e-16 * abs(L0) / h   # rounding floor of the central difference
         if name == "c":
             assert abs(fd) > 1e3 * noise   # the acid rate carries the signal
         print(f"{name}: fd {fd:.12e} adjoint {r['scalars'][q]:.12e} rel {abs(fd - r['scalars'][q]) / abs(fd):.3e}")
-        tol = 2e-3 if name == "D" else 1e-5
-        if abs(fd - r["scalars"][q]) > tol * abs(fd) + 10 * noise:
+        if abs(fd - r["scalars"][q]) > 3e-5 * abs(fd) + 10 * noise:
             bad.append((name, fd, r["scalars"][q], noise))
     assert not bad, bad
 
@@ -268,12 +265,12 @@ def test_adjoint_10k_steps_matches_oracle(torch, loss):
     and the four rate gradients -- is compared element by element with the
     oracle, both sides given the same seeds (the oracle's dL/dX^N).
 
-    v_misfit is the configured loss L = dx dy sum (V^N - V*)^2 / 2: every
-    output is held to 1e-5.  v_misfit_plus_w_mass adds dx dy sum W^N, a
+    v_misfit is the configured loss L = dx dy sum (V^N - V*)^2 / 2 (measured:
+    every output within 1.4e-7).  v_misfit_plus_w_mass adds dx dy sum W^N, a
     uniform source for lambda_W: the tensor gradients then come from
     differences of nearly equal lambda_W values, which keep the FP32 rounding
-    of the increments c lambda_W dt (about 1e-3 lambda_W per step); they are
-    held to 2e-5, the other outputs to 1e-5."""
+    of the increments c lambda_W dt (about 1e-3 lambda_W per step) (measured:
+    2.5e-6 for theta, 1.7e-6 for c).  Every output is held to 1e-5."""
     nx, steps = 128, 10000
     p = inputs.adjoint_2048(nx=nx, steps=steps)
     tg = inputs.adjoint_2048(nx=nx, steps=steps, target=True)
@@ -290,7 +287,7 @@ def test_adjoint_10k_steps_matches_oracle(torch, loss):
     with gg.GGSim.from_problem(p, precision="fp32_kahan", dt=s.dt) as sim:
         r = sim.adjoint(steps, None, t(gV), t(gW) if loss != "v_misfit" else None)
         assert sim.steps == steps
-    tensor_tol = 1e-5 if loss == "v_misfit" else 2e-5
+    tensor_tol = 1e-5
     for k, ref, tol in (("theta", gth, tensor_tol), ("lambda1", gl1, tensor_tol), ("lambda2", gl2, tensor_tol),
                         ("u0", lam0[0], 1e-5), ("v0", lam0[1], 1e-5), ("w0", lam0[2], 1e-5)):
         err = rel_err(r[k].cpu().numpy().astype(np.float64), ref)
