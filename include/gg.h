@@ -226,7 +226,7 @@ int gg_front_speed(gg_sim* sim, int32_t i0, int32_t j0, int64_t nsteps, double v
  *   checkpoint_every: steps between stored states (0 = about sqrt(nsteps)).
  * The forward pass is recomputed from stored checkpoints segment by segment
  * (sqrt(N) checkpointing); the states of the last segments, as many as fit
- * in 60 % of (this workspace's kept-state buffer + the free device memory),
+ * in 85 % of (this workspace's kept-state buffer + the free device memory),
  * are kept from the forward pass instead of recomputed.  The workspace
  * (checkpoints, recompute stash, kept states, adjoint fields) is allocated by
  * the first call, reused by later calls and freed by gg_adjoint_release or
@@ -349,21 +349,24 @@ int gg_batch_diagnostics(gg_batch* b, int32_t inst, gg_diag* out);
 
 /* Autotuner of the ensemble launch: times trial_steps steps (>= 1; 0 means
  * 8) of every candidate -- the launch mode (the persistent cooperative
- * kernel with a grid barrier between passes, or one launch of one warp per
+ * kernel with a grid barrier between passes, one launch of one warp per
+ * one-column tile per pass, or one launch of one warp per paired-column
  * tile per pass), steps per pass T in {1, 2, 3, 4} and chunk height by in
  * {32, 64, 128, 256} rows (by >= 4T + 8) of the warp tiles, whose strips are
- * 32 - 2T columns wide -- on the batch itself, keeps the fastest, and
- * restores the state it advanced.  chosen (may be NULL) receives {T, strip
- * width, by, threads per CTA (128: persistent mode, 32: passes mode)}.
- * Synchronizes. */
+ * 32 - 2T columns wide (one column per lane) or 60 / 56 of 64 (two columns
+ * per lane) -- on the batch itself, keeps the fastest, and restores the
+ * state it advanced.  chosen (may be NULL) receives {T, strip width, by,
+ * threads per CTA (128: persistent mode, 32: a per-pass mode)}; the mode
+ * itself is info[7] of gg_batch_launch_info.  Synchronizes. */
 int gg_batch_autotune(gg_batch* b, int64_t trial_steps, int32_t* chosen);
 
 /* Sets the ensemble launch plan directly: passes_mode 0 runs the persistent
- * cooperative kernel, 1 one launch per pass (one warp per tile, no grid
- * barrier; a step of at most 4096 passes is captured into one CUDA graph,
- * a longer one is launched directly); T in 1..4 steps per pass; chunk > 0
- * rows per tile (0 means 64).  Every plan computes the same bits.  Returns
- * GG_OK, GG_ERR_ARG or GG_ERR_OOM / GG_ERR_CUDA.  Synchronizes. */
+ * cooperative kernel, 1 one launch per pass (one warp per one-column tile,
+ * no grid barrier; a step of at most 4096 passes is captured into one CUDA
+ * graph, a longer one is launched directly), 2 the same with the
+ * paired-column tiles; T in 1..4 steps per pass; chunk > 0 rows per tile
+ * (0 means 64).  Every plan computes the same bits.  Returns GG_OK,
+ * GG_ERR_ARG or GG_ERR_OOM / GG_ERR_CUDA.  Synchronizes. */
 int gg_batch_set_plan(gg_batch* b, int32_t passes_mode, int32_t T, int32_t chunk);
 
 /* Testing hook for the bounded barrier wait: sets the per-wait time limit
@@ -380,7 +383,8 @@ int32_t gg_batch_steps_per_pass(const gg_batch* b);
  * T, strip width bx, chunk height by, threads per CTA, CTAs of the grid
  * (persistent mode: the persistent grid; passes mode: one per tile), work
  * items (tiles) per pass, 1 if the launch ran as a replayed CUDA graph (0 if
- * it was launched directly), and 1 for the passes mode (0 persistent).
+ * it was launched directly), and the mode of the plan (0 persistent, 1 one
+ * launch per pass with one-column tiles, 2 with paired-column tiles).
  * info must hold 8 int32. */
 int gg_batch_launch_info(const gg_batch* b, int32_t* info);
 double gg_batch_dt(const gg_batch* b, int32_t inst);

@@ -261,12 +261,15 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
     cudaError_t e = cudaSuccess;
 
     const Rates32 r = rates32(s);
-    // recompute depth and chunk height: the simulation's warp plan when it has
-    // one, else single steps
-    const bool warp_plan = s->plan.kind == 1 || s->plan.kind == 3;
-    const int TR = warp_plan ? s->plan.T : 1;
-    const int HR = warp_plan ? s->plan.by : default_plan(s->nx, s->ny, 1).by;
-    const bool paired = s->plan.kind == 3;
+    // Passes that also write the intermediate states (the kept segments'
+    // forward and the recomputation of the others) are HBM-bound with the
+    // extra state writes: they run the paired-column kernel four steps deep
+    // (24 B per cell-step against 28 for three), in chunks that fill whole
+    // waves of resident warps.  Every plan gives the same bits, so these
+    // states are exactly those of the simulation's own plan.
+    const int TR = 4;
+    const int HR = wave_chunk((s->nx + stepw2_out_columns(TR) - 1) / stepw2_out_columns(TR), s->ny,
+                              std::max(stepw2_wave_warps(TR, kahan), 152), 256);
     // Runs nsteps steps from the state `in` (u, v, w, cu, cv, cw) in passes of
     // up to TR steps.  The state after step kk (1 <= kk < nsteps, and nsteps
     // itself when fin is null) is written to slot(kk) (u, v, w); the last
@@ -301,14 +304,14 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
                 float* const* x = slot(kk + t);
                 sh.u[t - 1] = x[0]; sh.v[t - 1] = x[1]; sh.w[t - 1] = x[2];
             }
-            ee = paired ? launch_stepw2_stash(g, r, HR, Tp, kahan, sh, st) : launch_stepw_stash(g, r, HR, Tp, kahan, sh, st);
+            ee = launch_stepw2_stash(g, r, HR, Tp, kahan, sh, st);
             kk += Tp;
             ++pass;
         }
         return ee;
     };
 
-    // Trailing segments whose states fit in 60 % of the free device memory are
+    // Trailing segments whose states fit in 85 % of the free device memory are
     // kept from the forward pass and need no recomputation.
     int ns = 0;
     {
@@ -316,9 +319,9 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
         if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) { cudaGetLastError(); freeb = 0; }
         const size_t per_seg = (size_t)K * 3 * ((fbytes + 255) / 256 * 256);
         const size_t have = w->big_bytes;
-        // 60 % of (what this workspace already holds + what is free): the same
+        // 85 % of (what this workspace already holds + what is free): the same
         // budget on every call, so a second call reuses the first call's buffer
-        const size_t budget = (have + freeb) / 10 * 6;
+        const size_t budget = (have + freeb) / 20 * 17;
         ns = (int)std::min<size_t>((size_t)nseg, per_seg ? budget / per_seg : 0);
         const size_t need = (size_t)ns * per_seg;
         if (ns > 0 && need > have) {

@@ -11,6 +11,12 @@
 // generation word in global memory; a CTA that waits longer than the
 // barrier timeout sets the device error word and leaves, so a wait can
 // never hang the GPU: the next synchronizing call reports GG_ERR_TIMEOUT.
+//
+// Two more launch modes run the same work list as one ordinary launch per
+// pass (the kernel boundary orders the passes): with the one-column warp
+// tiles above, or with the tiles of the paired-column wavefront
+// (gg_stepw2.cuh: 64-column strips, two columns per lane, each warp with its
+// shared-memory row ring).
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -22,6 +28,7 @@
 
 #include "gg_sim.cuh"
 #include "gg_stepw.cuh"
+#include "gg_stepw2.cuh"
 
 using namespace gg;
 
@@ -142,6 +149,30 @@ __global__ void __launch_bounds__(32) pass_kernel(const InstDesc* __restrict__ d
     stepw::warp_pass_any<T, KAHAN>(sg, sr, H, it.y % strips, it.y / strips, threadIdx.x);
 }
 
+// The same pass with the paired-column tiles (one warp per tile, its
+// shared-memory ring as dynamic shared memory).
+extern __shared__ float2 g_batch_ring[];
+
+template <int T, bool KAHAN>
+__global__ void __launch_bounds__(32, T == 4 ? 12 : 1) pass2_kernel(const InstDesc* __restrict__ desc,
+                                                                    const int2* __restrict__ items, int nitems,
+                                                                    int parity, int variant, int H)
+{
+    const int w = blockIdx.x;
+    if (w >= nitems) return;
+    const int2 it = items[w];
+    const InstDesc& d = desc[it.x];
+    const int strips = d.strips[variant];
+    __shared__ Grid32 sg;
+    __shared__ Rates32 sr;
+    const int* gsrc = reinterpret_cast<const int*>(&d.g[parity]);
+    const int* rsrc = reinterpret_cast<const int*>(&d.r);
+    for (int k = threadIdx.x; k < (int)(sizeof(Grid32) / 4); k += 32) reinterpret_cast<int*>(&sg)[k] = gsrc[k];
+    for (int k = threadIdx.x; k < (int)(sizeof(Rates32) / 4); k += 32) reinterpret_cast<int*>(&sr)[k] = rsrc[k];
+    __syncwarp();
+    stepw2::warp_pass2_any<T, KAHAN>(sg, sr, H, it.y % strips, it.y / strips, threadIdx.x, g_batch_ring);
+}
+
 typedef void (*PassKernel)(const InstDesc*, const int2*, int, int, int, int);
 
 template <bool KAHAN>
@@ -152,6 +183,17 @@ PassKernel pick_pass(int T)
         case 2: return pass_kernel<2, KAHAN>;
         case 3: return pass_kernel<3, KAHAN>;
         default: return pass_kernel<4, KAHAN>;
+    }
+}
+
+template <bool KAHAN>
+PassKernel pick_pass2(int T)
+{
+    switch (T) {
+        case 1: return pass2_kernel<1, KAHAN>;
+        case 2: return pass2_kernel<2, KAHAN>;
+        case 3: return pass2_kernel<3, KAHAN>;
+        default: return pass2_kernel<4, KAHAN>;
     }
 }
 
@@ -171,9 +213,12 @@ BatchKernel pick(int T)
 
 constexpr int kBatchMaxT = 4;
 // Launch modes of the ensemble (Plan32::kind): the persistent cooperative
-// kernel with a grid barrier between passes, or one launch per pass.
+// kernel with a grid barrier between passes, or one launch per pass with the
+// one-column or the paired-column tiles.
 constexpr int kModePersistent = 1;
 constexpr int kModePasses = 2;
+constexpr int kModePasses2 = 3;
+inline bool per_pass(int mode) { return mode == kModePasses || mode == kModePasses2; }
 // A step of more passes than this in the passes mode is launched directly
 // instead of being captured into one graph.
 constexpr int64_t kMaxCapturedPasses = 4096;
@@ -223,7 +268,9 @@ void build_desc(gg_batch* b, std::vector<InstDesc>& desc, std::vector<int2> item
     desc.resize(b->n);
     items[0].clear();
     items[1].clear();
-    const int outs[2] = {32 - 2 * b->plan.T, 30};
+    const bool paired = b->plan.kind == kModePasses2;
+    const int outs[2] = {paired ? stepw2_out_columns(b->plan.T) : 32 - 2 * b->plan.T,
+                         paired ? stepw2_out_columns(1) : 30};
     for (int k = 0; k < b->n; ++k) {
         const InstHost& h = b->inst[k];
         InstDesc& d = desc[k];
@@ -297,7 +344,7 @@ BatchKernel kernel_for(const gg_batch* b, int T) { return b->kahan ? pick<true>(
 // kernel launches are enqueued.
 int prepare_kernels(gg_batch* b)
 {
-    if (b->plan.kind == kModePasses) return GG_OK;  // one CTA per work item, no persistent grid
+    if (per_pass(b->plan.kind)) return GG_OK;  // one CTA per work item, no persistent grid
     const int Ts[2] = {b->plan.T, 1};
     for (int v = 0; v < 2; ++v) {
         int ctas = 0;
@@ -313,12 +360,15 @@ int prepare_kernels(gg_batch* b)
 // (variant 0: the plan's T; variant 1: T = 1).
 int launch_passes(gg_batch* b, int T, int variant, int npasses, int parity0, cudaStream_t st)
 {
-    if (b->plan.kind == kModePasses) {
-        PassKernel pk = b->kahan ? pick_pass<true>(T) : pick_pass<false>(T);
+    if (per_pass(b->plan.kind)) {
+        const bool paired = b->plan.kind == kModePasses2;
+        PassKernel pk = paired ? (b->kahan ? pick_pass2<true>(T) : pick_pass2<false>(T))
+                               : (b->kahan ? pick_pass<true>(T) : pick_pass<false>(T));
+        const size_t smem = paired ? (b->kahan ? stepw2::Ring<true>::bytes : stepw2::Ring<false>::bytes) : 0;
         const int nit = b->nitems[variant];
         for (int p = 0; p < npasses; ++p) {
-            pk<<<std::max(nit, 1), 32, 0, st>>>(b->d_desc, b->d_items[variant], nit, (parity0 + p) & 1, variant,
-                                                b->plan.by);
+            pk<<<std::max(nit, 1), 32, smem, st>>>(b->d_desc, b->d_items[variant], nit, (parity0 + p) & 1, variant,
+                                                   b->plan.by);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return batch_fail(b, e, "batch pass launch");
         }
@@ -502,7 +552,7 @@ int gg_batch_step(gg_batch* b, int64_t nsteps)
     auto it = b->graphs.find(key);
     cudaError_t e = cudaSuccess;
     const int64_t npass = nsteps / b->plan.T + nsteps % b->plan.T;
-    const bool capturable = b->plan.kind != kModePasses || npass <= kMaxCapturedPasses;
+    const bool capturable = !per_pass(b->plan.kind) || npass <= kMaxCapturedPasses;
     if (it == b->graphs.end() && b->cap_stream && capturable) {
         // Capture the launches of this (nsteps, parity) once on the private
         // stream, replay the graph on the caller's stream afterwards.
@@ -549,7 +599,7 @@ int gg_batch_launch_info(const gg_batch* b, int32_t* info)
     info[4] = b->ctas;
     info[5] = b->nitems[0];
     info[6] = b->captured ? 1 : 0;
-    info[7] = b->plan.kind == kModePasses ? 1 : 0;
+    info[7] = b->plan.kind == kModePasses ? 1 : (b->plan.kind == kModePasses2 ? 2 : 0);
     return GG_OK;
 }
 
@@ -621,14 +671,15 @@ int gg_batch_autotune(gg_batch* b, int64_t trial_steps, int32_t* chosen)
     for (auto& h : b->inst) maxnx = std::max(maxnx, h.nx);
     // Candidates: steps per pass and chunk height of the warp tiles.
     std::vector<Plan32> cands;
-    for (int mode : {kModePersistent, kModePasses})
+    for (int mode : {kModePersistent, kModePasses, kModePasses2})
         for (int T = 1; T <= kBatchMaxT; ++T) {
             const std::vector<int> bys = {32, 64, 128, 256};
             for (int by : bys) {
                 if (by < 4 * T + 8) continue;
                 Plan32 p;
-                p.kind = mode; p.T = T; p.halo = T; p.bx = 32 - 2 * T; p.by = by;
-                p.threads = mode == kModePasses ? 32 : 128;
+                p.kind = mode; p.T = T; p.halo = T; p.by = by;
+                p.bx = mode == kModePasses2 ? stepw2_out_columns(T) : 32 - 2 * T;
+                p.threads = per_pass(mode) ? 32 : 128;
                 cands.push_back(p);
             }
         }
@@ -696,13 +747,14 @@ int gg_batch_autotune(gg_batch* b, int64_t trial_steps, int32_t* chosen)
 int gg_batch_set_plan(gg_batch* b, int32_t passes_mode, int32_t T, int32_t chunk)
 {
     if (!b) return GG_ERR_ARG;
-    if (T < 1 || T > kBatchMaxT || chunk < 0 || (passes_mode != 0 && passes_mode != 1)) {
-        b->last_error = "set_plan: T must be 1..4, chunk >= 0 and passes_mode 0 or 1";
+    if (T < 1 || T > kBatchMaxT || chunk < 0 || passes_mode < 0 || passes_mode > 2) {
+        b->last_error = "set_plan: T must be 1..4, chunk >= 0 and passes_mode 0, 1 or 2";
         return GG_ERR_ARG;
     }
     Plan32 p;
-    p.kind = passes_mode ? kModePasses : kModePersistent;
-    p.T = T; p.halo = T; p.bx = 32 - 2 * T;
+    p.kind = passes_mode == 2 ? kModePasses2 : (passes_mode == 1 ? kModePasses : kModePersistent);
+    p.T = T; p.halo = T;
+    p.bx = passes_mode == 2 ? stepw2_out_columns(T) : 32 - 2 * T;
     p.by = chunk > 0 ? chunk : 64;
     p.threads = passes_mode ? 32 : 128;
     return configure(b, p);

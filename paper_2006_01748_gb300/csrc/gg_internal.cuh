@@ -75,8 +75,6 @@ struct Stash32 {
     float* v[3];
     float* w[3];
 };
-cudaError_t launch_stepw_stash(const Grid32& g, const Rates32& r, int H, int T, bool kahan, const Stash32& st,
-                               cudaStream_t s);
 // Paired-column warp wavefront (two columns per lane, 64-column strips):
 // the same interface as launch_stepw / launch_stepw_stash / stepw_wave_warps,
 // and the columns a strip writes for T steps per pass.

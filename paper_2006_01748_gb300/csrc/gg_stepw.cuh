@@ -55,9 +55,9 @@ __device__ __forceinline__ float ld_state(const float* p)
 // EDGE: the strip touches the west or east domain boundary.  YEDGE: the
 // chunk's rows (with their halo of T rows) touch the south or north boundary;
 // interior chunks take every south / north face as present.
-template <int T, bool KAHAN, bool EDGE, bool COHERENT = false, bool STASH = false, bool YEDGE = true>
+template <int T, bool KAHAN, bool EDGE, bool COHERENT = false, bool YEDGE = true>
 __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, const int H, const int strip,
-                                          const int chunk, const int lane, const Stash32* stash = nullptr)
+                                          const int chunk, const int lane)
 {
     constexpr int OUT = 32 - 2 * T;
     // packed FP32 pairs for T >= 2 (issue-bound); the one-step pass is
@@ -240,16 +240,6 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
                     }
                 }
             } else {
-                if constexpr (STASH) {
-                    // intermediate level: also write the own rows and columns of step s0 + t
-                    if (q >= ys && q < hiT && outc) {
-                        const size_t o = (size_t)q * pitch + gx;
-                        const int li = (t < T) ? t - 1 : 0;
-                        stash->u[li][o] = uvn.x;
-                        stash->v[li][o] = uvn.y;
-                        stash->w[li][o] = wn;
-                    }
-                }
                 const int tt = (t < T) ? t : 0;  // level t passes row q on
                 sW[tt] = pW[tt]; pUV[tt] = nUV[tt]; pW[tt] = nW[tt];
                 nUV[tt] = uvn; nW[tt] = wn;
@@ -273,9 +263,9 @@ __device__ __forceinline__ void warp_pass(const Grid32& g, const Rates32& k, con
 // Runs warp_pass with the variant that matches the warp's position: interior
 // strips skip the east / west boundary handling, interior chunks the south /
 // north one.
-template <int T, bool KAHAN, bool COHERENT = false, bool STASH = false>
+template <int T, bool KAHAN, bool COHERENT = false>
 __device__ __forceinline__ void warp_pass_any(const Grid32& g, const Rates32& k, const int H, const int strip,
-                                              const int chunk, const int lane, const Stash32* stash = nullptr)
+                                              const int chunk, const int lane)
 {
     constexpr int OUT = 32 - 2 * T;
     const int gx0 = strip * OUT - T;
@@ -283,10 +273,10 @@ __device__ __forceinline__ void warp_pass_any(const Grid32& g, const Rates32& k,
     const int ys = chunk * H;
     const bool yin = ys - T >= 1 && ys + H + T <= g.ny - 1;
     if (xin) {
-        if (yin) warp_pass<T, KAHAN, false, COHERENT, STASH, false>(g, k, H, strip, chunk, lane, stash);
-        else warp_pass<T, KAHAN, false, COHERENT, STASH, true>(g, k, H, strip, chunk, lane, stash);
+        if (yin) warp_pass<T, KAHAN, false, COHERENT, false>(g, k, H, strip, chunk, lane);
+        else warp_pass<T, KAHAN, false, COHERENT, true>(g, k, H, strip, chunk, lane);
     } else {
-        warp_pass<T, KAHAN, true, COHERENT, STASH, true>(g, k, H, strip, chunk, lane, stash);
+        warp_pass<T, KAHAN, true, COHERENT, true>(g, k, H, strip, chunk, lane);
     }
 }
 

@@ -40,6 +40,8 @@ FIELDS = {"u": 0, "v": 1, "w": 2, "comp_u": 3, "comp_v": 4, "comp_w": 5, "a11": 
 # the paired-column warp wavefront (two columns per lane)
 PLAN_KINDS = {"smem": 0, "warp": 1, "warp2": 3}
 PLAN_NAMES = {0: "smem", 1: "warp", 2: "fp64", 3: "warp2"}
+# ensemble launch modes of gg_batch_set_plan / gg_batch_launch_info
+BATCH_MODES = ["persistent", "passes", "passes2"]
 
 GG_FLAG_NO_REACTION = 1
 GG_FLAG_ALLOW_UNSTABLE = 2
@@ -501,8 +503,7 @@ class GGBatch:
     def autotune(self, trial_steps: int = 8):
         chosen = (_I32 * 4)()
         self._check(lib().gg_batch_autotune(self._b, int(trial_steps), chosen), "gg_batch_autotune")
-        return dict(T=chosen[0], bx=chosen[1], by=chosen[2], threads=chosen[3],
-                    mode="passes" if chosen[3] == 32 else "persistent")
+        return dict(T=chosen[0], bx=chosen[1], by=chosen[2], threads=chosen[3], mode=self.launch_info()["mode"])
 
     def step(self, nsteps: int):
         self._check(lib().gg_batch_step(self._b, int(nsteps)), "gg_batch_step")
@@ -514,13 +515,13 @@ class GGBatch:
         info = (_I32 * 8)()
         self._check(lib().gg_batch_launch_info(self._b, info), "gg_batch_launch_info")
         return dict(T=info[0], bx=info[1], by=info[2], threads=info[3], ctas=info[4], tiles=info[5],
-                    graph=bool(info[6]), mode="passes" if info[7] else "persistent")
+                    graph=bool(info[6]), mode=BATCH_MODES[info[7]])
 
     def set_plan(self, mode: str = "persistent", T: int = 1, chunk: int = 0):
-        """mode "persistent" (cooperative kernel, grid barrier between passes)
-        or "passes" (one launch of one warp per tile per pass)."""
-        assert mode in ("persistent", "passes")
-        self._check(lib().gg_batch_set_plan(self._b, 1 if mode == "passes" else 0, int(T), int(chunk)),
+        """mode "persistent" (cooperative kernel, grid barrier between passes),
+        "passes" (one launch of one warp per one-column tile per pass) or
+        "passes2" (the same with the paired-column tiles)."""
+        self._check(lib().gg_batch_set_plan(self._b, BATCH_MODES.index(mode), int(T), int(chunk)),
                     "gg_batch_set_plan")
 
     def read(self, inst: int, field: str = "v", fp64: bool = True):

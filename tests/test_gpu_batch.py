@@ -30,7 +30,7 @@ def scaled_ensemble(n, scale, steps):
     return [inputs.ensemble_instance(k, specs[k], steps=steps, scale=scale) for k in range(n)]
 
 
-@pytest.mark.parametrize("mode", ["persistent", "passes"])
+@pytest.mark.parametrize("mode", ["persistent", "passes", "passes2"])
 @pytest.mark.parametrize("spp", [1, 2, 3, 4])
 def test_batch_matches_single_simulations_bitwise(spp, mode):
     probs = scaled_ensemble(12, 8, 37)
@@ -71,7 +71,7 @@ def test_autotune_restores_the_state():
         before = [b.read(k, "v") for k in range(6)]
         chosen = b.autotune(trial_steps=4)
         assert chosen["T"] in (1, 2, 3, 4) and chosen["bx"] == 32 - 2 * chosen["T"] and chosen["by"] > 0
-        assert chosen["mode"] in ("persistent", "passes")
+        assert chosen["mode"] in ("persistent", "passes", "passes2")
         for k in range(6):
             assert np.array_equal(b.read(k, "v"), before[k])
 
