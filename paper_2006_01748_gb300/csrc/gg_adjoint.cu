@@ -262,14 +262,15 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
 
     const Rates32 r = rates32(s);
     // Passes that also write the intermediate states (the kept segments'
-    // forward and the recomputation of the others) are HBM-bound with the
-    // extra state writes: they run the paired-column kernel four steps deep
-    // (24 B per cell-step against 28 for three), in chunks that fill whole
-    // waves of resident warps.  Every plan gives the same bits, so these
-    // states are exactly those of the simulation's own plan.
-    const int TR = 4;
-    const int HR = wave_chunk((s->nx + stepw2_out_columns(TR) - 1) / stepw2_out_columns(TR), s->ny,
-                              std::max(stepw2_wave_warps(TR, kahan), 152), 256);
+    // forward and the recomputation of the others) run the paired-column
+    // kernel with the simulation's depth and chunk height (at 2048^2 the tuned
+    // T = 3 with 42-row chunks took 21.6 us per step with the stash writes,
+    // four steps deep in whole waves 24.2 us), T = 3 when the plan is not a
+    // warp plan.  Every plan gives the same bits, so these states are exactly
+    // those of the simulation's own plan.
+    const bool warp_plan = s->plan.kind == 1 || s->plan.kind == 3;
+    const int TR = warp_plan ? s->plan.T : 3;
+    const int HR = warp_plan ? s->plan.by : default_plan(s->nx, s->ny, 3).by;
     // Runs nsteps steps from the state `in` (u, v, w, cu, cv, cw) in passes of
     // up to TR steps.  The state after step kk (1 <= kk < nsteps, and nsteps
     // itself when fin is null) is written to slot(kk) (u, v, w); the last
