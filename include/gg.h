@@ -223,11 +223,16 @@ int gg_front_speed(gg_sim* sim, int32_t i0, int32_t j0, int64_t nsteps, double v
  *     lambda1, lambda2) (chain rule through eq. (2)); may be NULL.
  *   g_u0, g_v0, g_w0: device, nx*ny floats: dL/d(U,V,W) at step 0; may be NULL.
  *   g_scalars: host, 4 doubles: dL/d(delta, rho, D, c); may be NULL.
- *   checkpoint_every: steps between stored states (0 = about sqrt(nsteps)).
- * The forward pass is recomputed from stored checkpoints segment by segment
- * (sqrt(N) checkpointing); the states of the last segments, as many as fit
- * in 85 % of (this workspace's kept-state buffer + the free device memory),
- * are kept from the forward pass instead of recomputed.  The workspace
+ *   checkpoint_every: steps between checkpoints (0 = about sqrt(nsteps)).
+ * The forward pass stores a checkpoint (state and Kahan terms) at the start
+ * of every segment of checkpoint_every steps; within a segment only the
+ * states at even steps are stored, and the reverse pass over a pair of steps
+ * rebuilds the state between two stored ones from the earlier (without its
+ * Kahan term: it differs from the forward's by its last rounding at most).
+ * The stored states of the last segments, as many as fit in 85 % of (this
+ * workspace's kept-state buffer + the free device memory), are kept from the
+ * forward pass; the others are recomputed from their checkpoints segment by
+ * segment (sqrt(N) checkpointing).  The workspace
  * (checkpoints, recompute stash, kept states, adjoint fields) is allocated by
  * the first call, reused by later calls and freed by gg_adjoint_release or
  * gg_destroy.  On return the simulation holds the state at step nsteps, as

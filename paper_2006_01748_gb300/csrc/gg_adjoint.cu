@@ -53,24 +53,29 @@ inline int wave_chunk(int strips, int ny, int cap, int hmax)
     const int nch = waves * per_wave;
     return std::min(hmax, std::max(hmin, (ny + nch - 1) / nch));
 }
-constexpr int kFlushEvery = 32;  // FP32 per-cell gradient sums are folded into FP64 this often
+constexpr int kFlushEvery = 64;  // FP32 per-cell gradient sums are folded into FP64 this often
 
-// The reverse passes (gg_adjoint2.cuh): paired columns, 64-column strips of
-// which 60 are written, one warp per CTA with its shared-memory ring.
+// The reverse passes (gg_adjoint2.cuh): paired columns, 64-column strips (60
+// columns written by the one-step pass, 56 by the two-step pass), one warp per
+// CTA with its shared-memory ring.
 extern __shared__ float2 g_adj_ring[];
 
+// The two-step pass carries three levels (the rebuilt forward step and two
+// reverse steps): capped at 192 registers it keeps 10 warps per SM without
+// spills (214 registers and 9 warps uncapped).
 template <int STEPS, bool KAHAN>
-__global__ void __launch_bounds__(32) adjw_kernel(const adjw::PassArgs a, const Rates32 k, const int H,
-                                                  const int nstrips, const int nwarps)
+__global__ void __maxnreg__(192) adjw_kernel(const adjw::PassArgs a, const Rates32 k, const int H, const int nstrips,
+                                             const int nwarps)
 {
     const int gw = blockIdx.x;
     if (gw >= nwarps) return;
     const int strip = gw % nstrips, chunk = gw / nstrips;
-    const int x0 = strip * 60 - 2;
+    const int x0 = strip * adjw::Geom<STEPS>::OUT - adjw::Geom<STEPS>::HLP;
     const int ys = chunk * H;
     double* part = a.partials + (size_t)gw * 4;
-    // interior chunks: every row the march touches has a south and a north face
-    const bool yin = ys - 3 >= 1 && ys + H + 3 <= a.ny - 1;
+    // interior chunks: every row the march touches (from five rows above the
+    // chunk to three below) has a south and a north face
+    const bool yin = ys - 5 >= 1 && ys + H + 3 <= a.ny - 1;
     if (x0 >= 1 && x0 + 63 <= a.nx - 2) {
         if (yin) adjw::march<STEPS, KAHAN, false, false>(a, k, H, strip, chunk, threadIdx.x, g_adj_ring, part);
         else adjw::march<STEPS, KAHAN, false, true>(a, k, H, strip, chunk, threadIdx.x, g_adj_ring, part);
@@ -79,7 +84,10 @@ __global__ void __launch_bounds__(32) adjw_kernel(const adjw::PassArgs a, const 
     }
 }
 
-inline int adjw_strips(int nx) { return (nx + 59) / 60; }
+template <int STEPS> inline int adjw_strips(int nx)
+{
+    return (nx + adjw::Geom<STEPS>::OUT - 1) / adjw::Geom<STEPS>::OUT;
+}
 
 // Resident warps of one wave of adjw_kernel<STEPS, KAHAN> (16 per SM if the
 // occupancy query fails).
@@ -104,7 +112,7 @@ template <int STEPS, bool KAHAN>
 AdjGeom adjw_geom(int nx, int ny)
 {
     AdjGeom g;
-    g.strips = adjw_strips(nx);
+    g.strips = adjw_strips<STEPS>(nx);
     g.H = wave_chunk(g.strips, ny, adjw_wave<STEPS, KAHAN>(), 128);
     g.warps = g.strips * ((ny + g.H - 1) / g.H);
     return g;
@@ -155,7 +163,8 @@ struct AdjWork {
     void* base = nullptr;
     int K = 0, nseg = 0, nstate = 0;
     std::vector<float*> ckpt;     // nseg x nstate fields
-    std::vector<float*> stash;    // K x 3 fields (slot 0 unused)
+    std::vector<float*> stash;    // (K - 1) / 2 states of 3 fields: the even offsets 2, 4, .. of a segment
+    float* scratch[3] = {};       // one state: the odd pass boundaries of a recomputation
     float* scomp[2][3] = {};      // Kahan terms of the recomputed states
     float* lam[2][6] = {};        // lam and its Kahan terms, ping-pong
     float* g32[3] = {};
@@ -194,7 +203,7 @@ static int adj_workspace(gg_sim* s, int K, int nseg, bool kahan, AdjWork** out)
     const int nstate = kahan ? 6 : 3;
     // one FP64 record of rate gradients per warp of the larger of the two adjoint launches
     const int nblocks = std::max(adj_geom(1, kahan, s->nx, s->ny).warps, adj_geom(2, kahan, s->nx, s->ny).warps);
-    const size_t need = fb * ((size_t)nseg * nstate + (size_t)K * 3 + 6 + 12 + 3) + db * 3 +
+    const size_t need = fb * ((size_t)nseg * nstate + (size_t)((K - 1) / 2) * 3 + 3 + 6 + 12 + 3) + db * 3 +
                         (((size_t)nblocks * 4 * 8 + 255) / 256 * 256);
     AdjWork* w = (AdjWork*)s->adj;
     if (w && w->bytes >= need && w->nstate == nstate) {
@@ -219,8 +228,9 @@ static int adj_workspace(gg_sim* s, int K, int nseg, bool kahan, AdjWork** out)
     char* p = (char*)w->base;
     w->ckpt.assign((size_t)nseg * nstate, nullptr);
     for (auto& f : w->ckpt) { f = (float*)p; p += fb; }
-    w->stash.assign((size_t)K * 3, nullptr);
+    w->stash.assign((size_t)((K - 1) / 2) * 3, nullptr);
     for (auto& f : w->stash) { f = (float*)p; p += fb; }
+    for (int f = 0; f < 3; ++f) { w->scratch[f] = (float*)p; p += fb; }
     for (int b = 0; b < 2; ++b)
         for (int f = 0; f < 3; ++f) { w->scomp[b][f] = (float*)p; p += fb; }
     for (int b = 0; b < 2; ++b)
@@ -272,11 +282,15 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
     const int TR = warp_plan ? s->plan.T : 3;
     const int HR = warp_plan ? s->plan.by : default_plan(s->nx, s->ny, 3).by;
     // Runs nsteps steps from the state `in` (u, v, w, cu, cv, cw) in passes of
-    // up to TR steps.  The state after step kk (1 <= kk < nsteps, and nsteps
-    // itself when fin is null) is written to slot(kk) (u, v, w); the last
-    // state goes to fin (u, v, w and Kahan terms) when fin is given.  Kahan
-    // terms between passes alternate between the two scomp buffers.
+    // up to TR steps.  Only the states at even steps are stored: the state
+    // after an even step kk (2 <= kk < nsteps, and nsteps itself when fin is
+    // null) is written to slot(kk) (u, v, w); a pass boundary at an odd step
+    // goes through the scratch state, and an intermediate level at an odd step
+    // writes nothing.  The last state goes to fin (u, v, w and Kahan terms)
+    // when fin is given.  Kahan terms between passes alternate between the two
+    // scomp buffers.
     auto passes = [&](float* const in[6], int nsteps, auto slot, float* const* fin) -> cudaError_t {
+        auto place = [&](int kk) -> float* const* { return (kk & 1) ? w->scratch : slot(kk); };
         int kk = 0, pass = 0;
         cudaError_t ee = cudaSuccess;
         while (kk < nsteps && ee == cudaSuccess) {
@@ -284,7 +298,7 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
             const bool last = kk + Tp == nsteps && fin;
             Grid32 g;
             if (kk == 0) { g.u = in[0]; g.v = in[1]; g.w = in[2]; }
-            else { float* const* x = slot(kk); g.u = x[0]; g.v = x[1]; g.w = x[2]; }
+            else { float* const* x = place(kk); g.u = x[0]; g.v = x[1]; g.w = x[2]; }
             g.cu = kahan ? (kk == 0 ? in[3] : w->scomp[pass & 1][0]) : nullptr;
             g.cv = kahan ? (kk == 0 ? in[4] : w->scomp[pass & 1][1]) : nullptr;
             g.cw = kahan ? (kk == 0 ? in[5] : w->scomp[pass & 1][2]) : nullptr;
@@ -292,7 +306,7 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
                 g.uo = fin[0]; g.vo = fin[1]; g.wo = fin[2];
                 g.cuo = kahan ? fin[3] : nullptr; g.cvo = kahan ? fin[4] : nullptr; g.cwo = kahan ? fin[5] : nullptr;
             } else {
-                float* const* x = slot(kk + Tp);
+                float* const* x = place(kk + Tp);
                 g.uo = x[0]; g.vo = x[1]; g.wo = x[2];
                 g.cuo = kahan ? w->scomp[(pass + 1) & 1][0] : nullptr;
                 g.cvo = kahan ? w->scomp[(pass + 1) & 1][1] : nullptr;
@@ -302,6 +316,7 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
             g.nx = s->nx; g.ny = s->ny; g.pitch = s->pitch;
             Stash32 sh = {};
             for (int t = 1; t < Tp; ++t) {
+                if ((kk + t) & 1) continue;  // odd steps are rebuilt by the reverse pass
                 float* const* x = slot(kk + t);
                 sh.u[t - 1] = x[0]; sh.v[t - 1] = x[1]; sh.w[t - 1] = x[2];
             }
@@ -318,7 +333,7 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
     {
         size_t freeb = 0, totalb = 0;
         if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) { cudaGetLastError(); freeb = 0; }
-        const size_t per_seg = (size_t)K * 3 * ((fbytes + 255) / 256 * 256);
+        const size_t per_seg = (size_t)((K - 1) / 2) * 3 * ((fbytes + 255) / 256 * 256);
         const size_t have = w->big_bytes;
         // 85 % of (what this workspace already holds + what is free): the same
         // budget on every call, so a second call reuses the first call's buffer
@@ -340,13 +355,15 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
     }
     const int seg_kept = nseg - ns;  // segments >= seg_kept are stored, not recomputed
     const size_t fstride = (fbytes + 255) / 256 * 256;
+    // the kept state at the even step kk >= 2 of segment seg
+    const int per_seg_states = (K - 1) / 2;
     auto big_slot = [&](int seg, int kk, float** out3) {
-        char* b = (char*)w->big + ((size_t)(seg - seg_kept) * K + kk) * 3 * fstride;
+        char* b = (char*)w->big + ((size_t)(seg - seg_kept) * per_seg_states + (kk / 2 - 1)) * 3 * fstride;
         out3[0] = (float*)b; out3[1] = (float*)(b + fstride); out3[2] = (float*)(b + 2 * fstride);
     };
 
     // 1. forward pass, storing the state (with Kahan terms) at the start of every
-    // segment and every state of the trailing segments
+    // segment and the states at even steps of the trailing segments
     for (int seg = 0; seg < nseg && e == cudaSuccess; ++seg) {
         for (int f = 0; f < nstate && e == cudaSuccess; ++f)
             e = cudaMemcpyAsync(w->ckpt[(size_t)seg * nstate + f], s->f32[s->cur][f], fbytes, cudaMemcpyDeviceToDevice, st);
@@ -394,40 +411,38 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
     for (int seg = nseg - 1; seg >= 0 && e == cudaSuccess; --seg) {
         const int len = (int)std::min<int64_t>(K, N - (int64_t)seg * K);
         const bool kept = seg >= seg_kept;
-        auto state = [&](int kk, int f) -> float* {  // u, v, w of X^{seg*K + kk}
+        auto state = [&](int kk, int f) -> float* {  // u, v, w of X^{seg*K + kk}, kk even
             if (kk == 0) return w->ckpt[(size_t)seg * nstate + f];
             if (kept) {
                 float* x[3];
                 big_slot(seg, kk, x);
                 return x[f];
             }
-            return w->stash[(size_t)kk * 3 + f];
+            return w->stash[(size_t)(kk / 2 - 1) * 3 + f];
         };
-        if (!kept && len > 1) {
-            // recompute X^{seg K + 1 .. seg K + len - 1} into the stash
+        if (!kept && len > 2) {
+            // recompute X^{seg K + 2, + 4 .. < seg K + len} into the stash
             float* in[6] = {state(0, 0), state(0, 1), state(0, 2),
                             kahan ? w->ckpt[(size_t)seg * nstate + 3] : nullptr,
                             kahan ? w->ckpt[(size_t)seg * nstate + 4] : nullptr,
                             kahan ? w->ckpt[(size_t)seg * nstate + 5] : nullptr};
             float* tmp[3];
             auto slot = [&](int kk) -> float* const* {
-                tmp[0] = w->stash[(size_t)kk * 3 + 0];
-                tmp[1] = w->stash[(size_t)kk * 3 + 1];
-                tmp[2] = w->stash[(size_t)kk * 3 + 2];
+                tmp[0] = w->stash[(size_t)(kk / 2 - 1) * 3 + 0];
+                tmp[1] = w->stash[(size_t)(kk / 2 - 1) * 3 + 1];
+                tmp[2] = w->stash[(size_t)(kk / 2 - 1) * 3 + 2];
                 return tmp;
             };
             e = passes(in, len - 1, slot, nullptr);
         }
-        // reverse sweep of the segment: an odd first step alone, then pairs of
-        // steps (kk, kk - 1) in one two-level pass
+        // reverse sweep of the segment: an odd first step alone (from the
+        // stored state at the even step len - 1), then pairs of steps
+        // (kk, kk - 1), kk odd, in one pass from the stored state kk - 1
         int kr = len - 1;
-        // one reverse pass from the state(s) kk (and kk - 1): lam[lb] -> lam[lb ^ 1]
-        auto pass_args = [&](int k1, int steps) {
+        // one reverse pass from the stored state k0 (even): lam[lb] -> lam[lb ^ 1]
+        auto pass_args = [&](int k0) {
             adjw::PassArgs a;
-            a.u1 = state(k1, 0); a.v1 = state(k1, 1); a.w1 = state(k1, 2);
-            a.u0 = steps == 2 ? state(k1 - 1, 0) : nullptr;
-            a.v0 = steps == 2 ? state(k1 - 1, 1) : nullptr;
-            a.w0 = steps == 2 ? state(k1 - 1, 2) : nullptr;
+            a.u = state(k0, 0); a.v = state(k0, 1); a.w = state(k0, 2);
             a.lu = w->lam[lb][0]; a.lv = w->lam[lb][1]; a.lw = w->lam[lb][2];
             a.clu = w->lam[lb][3]; a.clv = w->lam[lb][4]; a.clw = w->lam[lb][5];
             a.luo = w->lam[lb ^ 1][0]; a.lvo = w->lam[lb ^ 1][1]; a.lwo = w->lam[lb ^ 1][2];
@@ -439,7 +454,7 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
             return a;
         };
         auto single = [&](int k1) {
-            const adjw::PassArgs a = pass_args(k1, 1);
+            const adjw::PassArgs a = pass_args(k1);
             if (kahan) adjw_kernel<1, true><<<g1.warps, 32, adjw::kRingBytes, st>>>(a, r, g1.H, g1.strips, g1.warps);
             else adjw_kernel<1, false><<<g1.warps, 32, adjw::kRingBytes, st>>>(a, r, g1.H, g1.strips, g1.warps);
             lb ^= 1;
@@ -447,7 +462,7 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
             return cudaGetLastError();
         };
         auto pair = [&](int k1) {  // steps k1 and k1 - 1
-            const adjw::PassArgs a = pass_args(k1, 2);
+            const adjw::PassArgs a = pass_args(k1 - 1);
             if (kahan) adjw_kernel<2, true><<<g2.warps, 32, adjw::kRingBytes, st>>>(a, r, g2.H, g2.strips, g2.warps);
             else adjw_kernel<2, false><<<g2.warps, 32, adjw::kRingBytes, st>>>(a, r, g2.H, g2.strips, g2.warps);
             lb ^= 1;

@@ -285,15 +285,15 @@ struct RateSums2 {
     }
 };
 
-// Ring geometry: row r of the march in slot r & (kSlots - 1); rows r - 1 ..
+// Ring geometry: row r of the march in slot r & (kSlots - 1); rows r - 2 ..
 // r + kAhead are live at tick r.
-constexpr int kAhead = 2;
+constexpr int kAhead = 1;
 constexpr int kSlots = 4;
-// Fields of a slot (float2 rows of 32 lanes): the input row, then the
-// gradient sums of the row written when the slot is consumed.
+// Fields of a slot (float2 rows of 32 lanes): the input row (state, incoming
+// lambda with its Kahan terms, tensor weights), then the gradient sums of the
+// row written when the slot is consumed.
 enum : int {
-    F_U = 0, F_V, F_W, F_LV, F_LW, F_CLV, F_CLW, F_B, F_AY, F_LU, F_CLU, F_AX,
-    F_U0, F_V0, F_W0,  // two-step march: the state of the earlier step
+    F_U = 0, F_V, F_W, F_LU, F_LV, F_LW, F_CLU, F_CLV, F_CLW, F_AX, F_B, F_AY,
     F_G11, F_G12, F_G22,
     F_COUNT
 };
@@ -304,11 +304,11 @@ __device__ __forceinline__ void cp_async8(uint32_t dst, const float* src, int by
     stepw2::cp_async8(dst, src, bytes);
 }
 
-// Pointers of one reverse pass.  One step: state X^k in (u1, v1, w1) and
-// lambda^{k+1} in (lu ... clw); two steps: X^{k+1} in (u1, v1, w1), X^k in
-// (u0, v0, w0), lambda^{k+2} in (lu ... clw).  Output lambda in (luo ...).
+// Pointers of one reverse pass: the stored state X^k in (u, v, w), the
+// incoming lambda (lambda^{k+1} for one step, lambda^{k+2} for two) in
+// (lu ... clw), the outgoing lambda^k in (luo ...).
 struct PassArgs {
-    const float *u1, *v1, *w1, *u0, *v0, *w0;
+    const float *u, *v, *w;
     const float *lu, *lv, *lw, *clu, *clv, *clw;
     float *luo, *lvo, *lwo, *cluo, *clvo, *clwo;
     const float *ax, *b, *ay;
@@ -317,19 +317,167 @@ struct PassArgs {
     int nx, ny, pitch;
 };
 
-// The reverse march of one warp: STEPS = 1 or 2 levels.  Level 1 computes
-// row r - 1 at tick r, level 2 row r - 2 (from level 1's lambda, which never
-// leaves registers).  Each march starts two rows above its first written row
-// so that the carries of that row are complete.
+// Strip geometry of the marches: STEPS = 1 reverse level (halo 1, rounded up
+// to a pair), STEPS = 2 the forward level and two reverse levels (halo 3).
+template <int STEPS> struct Geom {
+    static constexpr int HLP = STEPS == 1 ? 2 : 4;
+    static constexpr int OUT = 64 - 2 * HLP;
+};
+
+// What the forward level passes from one row to the next (the carries of
+// gg_stepw2.cuh's march): the north faces of the previous row and the east w
+// and y cross term of the own row.
+struct FwdCarry {
+    float2 G, H, WE, Z;
+};
+
+// One explicit Euler step of eq. (3) at row q of a pair, without Kahan terms:
+// the face fluxes of Tables 1 and 2 from rows q (P) and q+1 (N) and w of row
+// q-1, as in gg_stepw2.cuh.  It rebuilds the state X^{k+1} of the step the
+// two-level reverse march needs from the stored X^k; the rebuilt state
+// differs from the forward pass's compensated one by the last rounding only.
+template <bool EDGE, bool YEDGE>
+__device__ __forceinline__ void fwd_level(const Rates32& k, float2 bP, float2 bN, float2 ax, float2 ay, float2 u,
+                                          float2 v, float2 w, float2 un, float2 vn, float2 wn, float2 wS,
+                                          FwdCarry& c, const Mask& m, bool hasS_, bool hasN_, float2& uo,
+                                          float2& vo, float2& wo)
+{
+    const bool hasS = YEDGE ? hasS_ : true, hasN = YEDGE ? hasN_ : true;
+    const float2 z = make_float2(0.0f, 0.0f), one = dup(1.0f);
+    // x cross term of the own row (tangential difference mirrored at the south / north boundary)
+    const float2 zxP = mul2(bP, sub2(hasN ? wn : w, hasS ? wS : w));
+    float2 uE = east_of(u), vE = east_of(v), wNE = east_of(wn), wNW = west_of(wn);
+    const float2 zxE = east_of(zxP);
+    mask_e<EDGE>(uE, u, m);
+    mask_e<EDGE>(vE, v, m);
+    mask_e<EDGE>(wNE, wn, m);
+    mask_w<EDGE>(wNW, wn, m);
+    const float2 wE = c.WE;
+    c.WE = wNE;
+    const float2 zyP = c.Z, zyN = mul2(bN, sub2(wNE, wNW));
+    c.Z = zyN;
+    // east and north faces: acid a (W_R - W_L) + (z_L + z_R), tumour (K - K/2 (U_L + U_R)) (V_R - V_L)
+    float2 gE = fma2(ax, sub2(wE, w), add2(zxP, zxE));
+    float2 hE = mul2(fma2(dup(-k.hKx), add2(u, uE), dup(k.Kx)), sub2(vE, v));
+    float2 gN = fma2(ay, sub2(wn, w), add2(zyP, zyN));
+    float2 hN = mul2(fma2(dup(-k.hKy), add2(u, un), dup(k.Ky)), sub2(vn, v));
+    mask_e<EDGE>(gE, z, m);
+    mask_e<EDGE>(hE, z, m);
+    if (!hasN) { gN = z; hN = z; }
+    float2 gW = west_of(gE), hW = west_of(hE);
+    mask_w<EDGE>(gW, z, m);
+    mask_w<EDGE>(hW, z, m);
+    const float2 gS = hasS ? c.G : z, hS = hasS ? c.H : z;
+    c.G = gN;
+    c.H = hN;
+    const float2 d1 = add2(sub2(hE, hW), sub2(hN, hS));
+    const float2 d2 = add2(sub2(gE, gW), sub2(gN, gS));
+    float2 fu, fv, fw;
+    if (k.no_reaction) {
+        fu = z;
+        fv = d1;
+        fw = d2;
+    } else {
+        fu = mul2(u, fma2(dup(-k.delta), w, sub2(one, u)));
+        fv = fma2(mul2(dup(k.rho), v), sub2(one, v), d1);
+        fw = fma2(dup(k.c), sub2(v, w), d2);
+    }
+    const float2 dt = dup(k.dt);
+    uo = fma2(dt, fu, u);
+    vo = fma2(dt, fv, v);
+    wo = fma2(dt, fw, w);
+}
+
+// Shared helpers of the marches: the slot of row r, the copy of one input
+// row (and of the gradient sums of output row qg) into it, and the store of
+// an output row.
+struct RingIO {
+    float2* rl;  // this lane's entry of slot 0
+    const float* src[12];
+    int cpb;
+    size_t coff;
+    __device__ __forceinline__ float2* slot(int r) const { return rl + (r & (kSlots - 1)) * F_COUNT * 32; }
+};
+
+template <bool KAHAN>
+__device__ __forceinline__ void fetch_row(const RingIO& io, const PassArgs& a, int r, int qg, bool copy_in,
+                                          bool copy_g, int ny, int pitch, int ca)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(io.slot(r));
+    if (copy_in) {
+        const bool in = r >= 0 && r < ny;  // zeros outside the domain
+        const size_t o = (size_t)(in ? r : 0) * pitch + io.coff;
+#pragma unroll
+        for (int f = 0; f < 12; ++f) {
+            if (!KAHAN && (f == F_CLU || f == F_CLV || f == F_CLW)) continue;
+            cp_async8(d + f * 256, io.src[f] + o, in ? io.cpb : 0);
+        }
+    }
+    if (copy_g) {
+        const size_t og = (size_t)qg * pitch + ca;
+        cp_async8(d + F_G11 * 256, a.g11 + og, io.cpb);
+        cp_async8(d + F_G12 * 256, a.g12 + og, io.cpb);
+        cp_async8(d + F_G22 * 256, a.g22 + og, io.cpb);
+    }
+    stepw2::cp_async_commit();
+}
+
+template <bool KAHAN, bool EDGE>
+__device__ __forceinline__ void store_row(const PassArgs& a, const Out& o, float2 g11, float2 g12, float2 g22,
+                                          size_t off, bool b_in)
+{
+    if (!EDGE || b_in) {
+        *reinterpret_cast<float2*>(a.luo + off) = o.lu;
+        *reinterpret_cast<float2*>(a.lvo + off) = o.lv;
+        *reinterpret_cast<float2*>(a.lwo + off) = o.lw;
+        if (KAHAN) {
+            *reinterpret_cast<float2*>(a.cluo + off) = o.clu;
+            *reinterpret_cast<float2*>(a.clvo + off) = o.clv;
+            *reinterpret_cast<float2*>(a.clwo + off) = o.clw;
+        }
+        *reinterpret_cast<float2*>(a.g11 + off) = g11;
+        *reinterpret_cast<float2*>(a.g12 + off) = g12;
+        *reinterpret_cast<float2*>(a.g22 + off) = g22;
+    } else {
+        a.luo[off] = o.lu.x; a.lvo[off] = o.lv.x; a.lwo[off] = o.lw.x;
+        if (KAHAN) { a.cluo[off] = o.clu.x; a.clvo[off] = o.clv.x; a.clwo[off] = o.clw.x; }
+        a.g11[off] = g11.x; a.g12[off] = g12.x; a.g22[off] = g22.x;
+    }
+}
+
+__device__ __forceinline__ Row ring_row(const float2* s, bool kahan)
+{
+    Row x;
+    x.u = s[F_U * 32]; x.v = s[F_V * 32]; x.w = s[F_W * 32];
+    x.lv = s[F_LV * 32]; x.lw = s[F_LW * 32];
+    if (kahan) { x.clv = s[F_CLV * 32]; x.clw = s[F_CLW * 32]; }
+    else { x.clv = x.clw = make_float2(0.0f, 0.0f); }
+    x.b = s[F_B * 32]; x.ay = s[F_AY * 32];
+    return x;
+}
+
+// One reverse step as a warp march (STEPS = 1): the level computes row r - 1
+// at tick r from input rows r - 1 and r of the ring (lambda^{k+1}, the stored
+// X^k, the tensor); the march starts two rows above its first written row so
+// that the carries of that row are complete.
+//
+// Two reverse steps (STEPS = 2, steps k + 1 and k from the stored X^k and
+// lambda^{k+2}): at tick r the forward level F rebuilds row r - 1 of X^{k+1}
+// from rows r - 2 .. r of X^k, level A1 computes row r - 2 of lambda^{k+1}
+// from X^{k+1} (rows r - 3 .. r - 1, kept in registers) and lambda^{k+2}
+// (rows r - 2, r - 1 of the ring), level A2 row r - 3 of lambda^k from X^k
+// (rows r - 4 .. r - 2) and A1's lambda^{k+1}; so only every other state is
+// stored, and of the two states of the step pair only X^k crosses HBM.  Rows
+// that a level has moved past stay in registers (the tensor and X^k rows of
+// A2, the X^{k+1} rows of A1), so the ring holds rows r - 2 .. r + 1 only.
 template <int STEPS, bool KAHAN, bool EDGE, bool YEDGE>
 __device__ __forceinline__ void march(const PassArgs& a, const Rates32& kr, const int H, const int strip,
                                       const int chunk, const int lane, float2* ring, double* part)
 {
+    static_assert(STEPS == 1 || STEPS == 2, "one or two reverse steps");
     const K2 k = make_k2(kr);
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
-    constexpr int HL = STEPS;  // halo columns
-    constexpr int HLP = (HL + 1) / 2 * 2;
-    constexpr int OUT = 64 - 2 * HLP;
+    constexpr int HLP = Geom<STEPS>::HLP, OUT = Geom<STEPS>::OUT;
     const int ca = strip * OUT - HLP + 2 * lane;
     const int cb = ca + 1;
     const bool ld_ok = EDGE ? (ca >= 0 && ca < nx) : true;
@@ -338,122 +486,109 @@ __device__ __forceinline__ void march(const PassArgs& a, const Rates32& kr, cons
     const bool outc = lane >= HLP / 2 && lane < 32 - HLP / 2 && ld_ok;
     const int ys = chunk * H;
     const int ye = min(ny, ys + H);
-    // first tick: level STEPS computes row r0 - STEPS = ys - 2 (clipped at -1 / 0)
-    const int r0 = STEPS == 2 ? max(0, ys - 2) : max(0, ys - 1);
-    const int r1 = ye + STEPS;  // one past the last tick
-    const int cpb = !EDGE ? 8 : (!ld_ok ? 0 : (b_in ? 8 : 4));
-    const size_t coff = ld_ok ? (size_t)ca : 0;
+    // the written row of tick r is r - STEPS - (STEPS == 2): r - 1 or r - 3
+    constexpr int LAG = STEPS == 1 ? 1 : 3;
+    const int r0 = STEPS == 1 ? max(0, ys - 1) : max(0, ys - 2);
+    const int r1 = ye + LAG;  // one past the last tick
 
-    float2* const rl = ring + lane;
-    auto slot = [&](int r) { return rl + (r & (kSlots - 1)) * F_COUNT * 32; };
-    const float* const src[15] = {a.u1, a.v1, a.w1, a.lv, a.lw, a.clv, a.clw, a.b, a.ay, a.lu, a.clu, a.ax,
-                                  a.u0, a.v0, a.w0};
-    constexpr int NIN = STEPS == 2 ? 15 : 12;
-    auto fetch = [&](int r) {
-        const uint32_t d = (uint32_t)__cvta_generic_to_shared(slot(r));
-        if (r < r1) {
-            // input row r (zeros outside the domain)
-            const bool in = r >= 0 && r < ny;
-            const size_t o = (size_t)(in ? r : 0) * pitch + coff;
+    RingIO io;
+    io.rl = ring + lane;
+    io.cpb = !EDGE ? 8 : (!ld_ok ? 0 : (b_in ? 8 : 4));
+    io.coff = ld_ok ? (size_t)ca : 0;
+    const float* src[12] = {a.u, a.v, a.w, a.lu, a.lv, a.lw, a.clu, a.clv, a.clw, a.ax, a.b, a.ay};
 #pragma unroll
-            for (int f = 0; f < NIN; ++f) {
-                if (!KAHAN && (f == F_CLV || f == F_CLW || f == F_CLU)) continue;
-                cp_async8(d + f * 256, src[f] + o, in ? cpb : 0);
-            }
-            // gradient sums of the row written at tick r
-            const int qg = r - STEPS;
-            if (qg >= ys && qg < ye && outc) {
-                const size_t og = (size_t)qg * pitch + ca;
-                cp_async8(d + F_G11 * 256, a.g11 + og, cpb);
-                cp_async8(d + F_G12 * 256, a.g12 + og, cpb);
-                cp_async8(d + F_G22 * 256, a.g22 + og, cpb);
-            }
-        }
-        stepw2::cp_async_commit();
-    };
-    auto row = [&](const float2* s) {
-        Row x;
-        x.u = s[F_U * 32]; x.v = s[F_V * 32]; x.w = s[F_W * 32];
-        x.lv = s[F_LV * 32]; x.lw = s[F_LW * 32];
-        if (KAHAN) { x.clv = s[F_CLV * 32]; x.clw = s[F_CLW * 32]; }
-        else { x.clv = x.clw = make_float2(0.0f, 0.0f); }
-        x.b = s[F_B * 32]; x.ay = s[F_AY * 32];
-        return x;
+    for (int f = 0; f < 12; ++f) io.src[f] = src[f];
+    auto fetch = [&](int r) {
+        const int qg = r - LAG;
+        fetch_row<KAHAN>(io, a, r, qg, r < r1, r < r1 && qg >= ys && qg < ye && outc, ny, pitch, ca);
     };
 
     const float2 z = make_float2(0.0f, 0.0f);
     RateSums2 sums;
     Carry c1{z, z, z, z, z, z, z, z, z}, c2{z, z, z, z, z, z, z, z, z};
-    float2 S1w = z;                       // level 1: w of row r - 2
-    // level 2 (two steps): its own row r - 2 carried from the last tick
-    float2 u0P = z, v0P = z, w0P = z, S2w = z;        // X^k of rows r - 2 (and w of r - 3)
-    float2 lvP = z, lwP = z, clvP = z, clwP = z, luP = z, cluP = z;  // lambda^{k+1} of row r - 2
-    float2 bP = z, ayP = z, axP = z;                 // tensor of row r - 2
-    float2 d11c = z, d12c = z, d22c = z;             // level 1's increments of row r - 2
+    FwdCarry cf{z, z, z, z};
+    float2 S1w = z;  // STEPS 1: w of row r - 2; STEPS 2: X^{k+1} w of row r - 3
+    // STEPS 2: X^{k+1} of row r - 2 (F's last output), X^k of rows r - 3 and
+    // w of r - 4, lambda^{k+1} of row r - 3, tensor rows of A1 (r - 2) and A2
+    // (r - 3), A1's increments of row r - 3
+    float2 xuP = z, xvP = z, xwP = z;
+    float2 u0P = z, v0P = z, w0P = z, S2w = z;
+    float2 lvP = z, lwP = z, clvP = z, clwP = z, luP = z, cluP = z;
+    float2 ax1 = z, b1 = z, ay1 = z, ax2 = z, b2 = z, ay2 = z;
+    float2 d11c = z, d12c = z, d22c = z;
 
-    // rows r0 - 1 .. r0 + kAhead - 1 in flight before the first tick
+    // rows r0 - 2 .. r0 + kAhead - 1 in flight before the first tick
 #pragma unroll
-    for (int i = -1; i < kAhead; ++i) fetch(r0 + i);
+    for (int i = -2; i < kAhead; ++i) fetch(r0 + i);
     for (int r = r0; r < r1; ++r) {
         fetch(r + kAhead);
         stepw2::cp_async_wait<kAhead>();  // rows up to r have landed
-        const float2* sP = slot(r - 1);
-        const float2* sN = slot(r);
-        const Row P1 = row(sP), N1 = row(sN);
-        const float2 lu1 = sP[F_LU * 32], clu1 = KAHAN ? sP[F_CLU * 32] : z, ax1 = sP[F_AX * 32];
-        const int q1 = r - 1;
-        const Out o1 = adj_level2<KAHAN, EDGE, YEDGE>(k, S1w, P1, N1, lu1, clu1, ax1, m, q1 > 0, q1 + 1 < ny, c1);
-        S1w = P1.w;
-        Out o;        // the result written at this tick
-        int qw;       // its row
-        float2 dc1 = z, dc2 = z, dc3 = z;  // increments of the other level, same row
-        if constexpr (STEPS == 2) {
-            const int q2 = r - 2;
+        const float2* s0 = io.slot(r);
+        const float2* s1 = io.slot(r - 1);
+        Out o;
+        int qw;
+        float2 dc1 = z, dc2 = z, dc3 = z;
+        if constexpr (STEPS == 1) {
+            const Row P = ring_row(s1, KAHAN), N = ring_row(s0, KAHAN);
+            const float2 lu = s1[F_LU * 32], clu = KAHAN ? s1[F_CLU * 32] : z, ax = s1[F_AX * 32];
+            const int q = r - 1;
+            o = adj_level2<KAHAN, EDGE, YEDGE>(k, S1w, P, N, lu, clu, ax, m, q > 0, q + 1 < ny, c1);
+            S1w = P.w;
+            qw = q;
+        } else {
+            const float2* s2 = io.slot(r - 2);
+            // F: row r - 1 of X^{k+1} from X^k rows r - 2 (w), r - 1, r
+            const float2 axF = s1[F_AX * 32], bF = s1[F_B * 32], ayF = s1[F_AY * 32], bNF = s0[F_B * 32];
+            float2 xu, xv, xw;
+            const int qf = r - 1;
+            fwd_level<EDGE, YEDGE>(kr, bF, bNF, axF, ayF, s1[F_U * 32], s1[F_V * 32], s1[F_W * 32], s0[F_U * 32],
+                                   s0[F_V * 32], s0[F_W * 32], s2[F_W * 32], cf, m, qf > 0, qf + 1 < ny, xu, xv,
+                                   xw);
+            // A1: row r - 2 of lambda^{k+1} (step k + 1, state X^{k+1})
+            const int q1 = r - 2;
+            Row P1, N1;
+            P1.u = xuP; P1.v = xvP; P1.w = xwP;
+            P1.lv = s2[F_LV * 32]; P1.lw = s2[F_LW * 32];
+            if (KAHAN) { P1.clv = s2[F_CLV * 32]; P1.clw = s2[F_CLW * 32]; }
+            else { P1.clv = P1.clw = z; }
+            P1.b = b1; P1.ay = ay1;
+            N1.u = xu; N1.v = xv; N1.w = xw;
+            N1.lv = s1[F_LV * 32]; N1.lw = s1[F_LW * 32];
+            if (KAHAN) { N1.clv = s1[F_CLV * 32]; N1.clw = s1[F_CLW * 32]; }
+            else { N1.clv = N1.clw = z; }
+            N1.b = bF; N1.ay = ayF;
+            const float2 lu1 = s2[F_LU * 32], clu1 = KAHAN ? s2[F_CLU * 32] : z;
+            const Out o1 = adj_level2<KAHAN, EDGE, YEDGE>(k, S1w, P1, N1, lu1, clu1, ax1, m, q1 > 0, q1 + 1 < ny, c1);
+            // A2: row r - 3 of lambda^k (step k, state X^k)
+            const int q2 = r - 3;
             Row P2, N2;
             P2.u = u0P; P2.v = v0P; P2.w = w0P;
             P2.lv = lvP; P2.lw = lwP; P2.clv = clvP; P2.clw = clwP;
-            P2.b = bP; P2.ay = ayP;
-            N2.u = sP[F_U0 * 32]; N2.v = sP[F_V0 * 32]; N2.w = sP[F_W0 * 32];
+            P2.b = b2; P2.ay = ay2;
+            N2.u = s2[F_U * 32]; N2.v = s2[F_V * 32]; N2.w = s2[F_W * 32];
             N2.lv = o1.lv; N2.lw = o1.lw; N2.clv = o1.clv; N2.clw = o1.clw;
-            N2.b = P1.b; N2.ay = P1.ay;
-            o = adj_level2<KAHAN, EDGE, YEDGE>(k, S2w, P2, N2, luP, cluP, axP, m, q2 > 0, q2 + 1 < ny, c2);
+            N2.b = b1; N2.ay = ay1;
+            o = adj_level2<KAHAN, EDGE, YEDGE>(k, S2w, P2, N2, luP, cluP, ax2, m, q2 > 0, q2 + 1 < ny, c2);
             qw = q2;
             dc1 = d11c; dc2 = d12c; dc3 = d22c;
-            // level 1's rate terms of its own row count where the row is the chunk's
+            // A1's rate terms count where its row is the chunk's
             if (q1 >= ys && q1 < ye && outc) sums.add_all(o1);
-            // row r - 1 becomes level 2's own row at the next tick
-            S2w = w0P;
-            u0P = N2.u; v0P = N2.v; w0P = N2.w;
+            // rows move on: F's row r - 1 becomes A1's own row, X^k row r - 2
+            // and A1's lambda row r - 2 become A2's own row
+            S1w = xwP; xuP = xu; xvP = xv; xwP = xw;
+            S2w = w0P; u0P = N2.u; v0P = N2.v; w0P = N2.w;
             lvP = o1.lv; lwP = o1.lw; clvP = o1.clv; clwP = o1.clw; luP = o1.lu; cluP = o1.clu;
-            bP = P1.b; ayP = P1.ay; axP = ax1;
+            ax2 = ax1; b2 = b1; ay2 = ay1;
+            ax1 = axF; b1 = bF; ay1 = ayF;
             d11c = o1.d11; d12c = o1.d12; d22c = o1.d22;
-        } else {
-            o = o1;
-            qw = q1;
         }
         if (qw >= ys && qw < ye && outc) {
             sums.add_all(o);
             const size_t off = (size_t)qw * pitch + ca;
-            const float2 g11 = add2(sN[F_G11 * 32], add2(dc1, o.d11));
-            const float2 g12 = add2(sN[F_G12 * 32], add2(dc2, o.d12));
-            const float2 g22 = add2(sN[F_G22 * 32], add2(dc3, o.d22));
-            if (!EDGE || b_in) {
-                *reinterpret_cast<float2*>(a.luo + off) = o.lu;
-                *reinterpret_cast<float2*>(a.lvo + off) = o.lv;
-                *reinterpret_cast<float2*>(a.lwo + off) = o.lw;
-                if (KAHAN) {
-                    *reinterpret_cast<float2*>(a.cluo + off) = o.clu;
-                    *reinterpret_cast<float2*>(a.clvo + off) = o.clv;
-                    *reinterpret_cast<float2*>(a.clwo + off) = o.clw;
-                }
-                *reinterpret_cast<float2*>(a.g11 + off) = g11;
-                *reinterpret_cast<float2*>(a.g12 + off) = g12;
-                *reinterpret_cast<float2*>(a.g22 + off) = g22;
-            } else {
-                a.luo[off] = o.lu.x; a.lvo[off] = o.lv.x; a.lwo[off] = o.lw.x;
-                if (KAHAN) { a.cluo[off] = o.clu.x; a.clvo[off] = o.clv.x; a.clwo[off] = o.clw.x; }
-                a.g11[off] = g11.x; a.g12[off] = g12.x; a.g22[off] = g22.x;
-            }
+            const float2 g11 = add2(s0[F_G11 * 32], add2(dc1, o.d11));
+            const float2 g12 = add2(s0[F_G12 * 32], add2(dc2, o.d12));
+            const float2 g22 = add2(s0[F_G22 * 32], add2(dc3, o.d22));
+            store_row<KAHAN, EDGE>(a, o, g11, g12, g22, off, b_in);
         }
     }
     stepw2::cp_async_wait<0>();  // nothing in flight when the warp leaves

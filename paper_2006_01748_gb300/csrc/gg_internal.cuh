@@ -68,16 +68,18 @@ cudaError_t launch_stepw(const Grid32& g, const Rates32& r, int H, int T, bool k
 int stepw_wave_warps(int T, bool kahan);
 
 // Destinations of the intermediate time levels of a pass (level t = 1..T-1
-// writes u, v, w of step s0 + t to u[t-1], v[t-1], w[t-1]); used to
-// recompute every state of an adjoint segment in passes of T steps.
+// writes u, v, w of step s0 + t to u[t-1], v[t-1], w[t-1]; a level with null
+// destinations writes nothing); used to store the states of an adjoint
+// segment in passes of T steps.
 struct Stash32 {
     float* u[3];
     float* v[3];
     float* w[3];
 };
 // Paired-column warp wavefront (two columns per lane, 64-column strips):
-// the same interface as launch_stepw / launch_stepw_stash / stepw_wave_warps,
-// and the columns a strip writes for T steps per pass.
+// the same interface as launch_stepw / stepw_wave_warps, a variant that also
+// writes the intermediate levels, and the columns a strip writes for T steps
+// per pass.
 cudaError_t launch_stepw2(const Grid32& g, const Rates32& r, int H, int T, bool kahan, cudaStream_t s);
 cudaError_t launch_stepw2_stash(const Grid32& g, const Rates32& r, int H, int T, bool kahan, const Stash32& st,
                                 cudaStream_t s);

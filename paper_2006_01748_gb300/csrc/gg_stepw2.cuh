@@ -75,7 +75,8 @@ template <int N> __device__ __forceinline__ void cp_async_wait()
 
 // EDGE: the strip touches the west or east domain boundary.  YEDGE: the
 // chunk's rows (with their halo of T rows) touch the south or north
-// boundary.  STASH: levels 1..T-1 also write u, v, w of their own rows.
+// boundary.  STASH: levels 1..T-1 also write u, v, w of their own rows (those
+// with a non-null destination).
 // ring: this warp's Ring<KAHAN>::bytes of shared memory.  The ring is read
 // with ordinary shared-memory loads, which the compiler keeps in program order
 // with the cp.async copies (their asm statements clobber memory); a slot is
@@ -260,9 +261,10 @@ __device__ __forceinline__ void warp_pass2(const Grid32& g, const Rates32& k, co
             } else {
                 if constexpr (STASH) {
                     // intermediate level: also write the own rows of step s0 + t
-                    if (q >= ys && q < hiT && outp) {
+                    // (a level whose destination is null writes nothing)
+                    const int li = (t < T) ? t - 1 : 0;
+                    if (q >= ys && q < hiT && outp && stash->u[li]) {
                         const size_t o = (size_t)q * pitch + ca;
-                        const int li = (t < T) ? t - 1 : 0;
                         if (!EDGE || b_in) {
                             *reinterpret_cast<float2*>(stash->u[li] + o) = uo;
                             *reinterpret_cast<float2*>(stash->v[li] + o) = vo;

@@ -108,21 +108,26 @@ def test_adjoint_without_kahan_and_without_reactions(torch):
 
 
 def test_checkpoint_spacing_does_not_change_the_result(torch):
-    """The recomputed states are bitwise those of the forward pass for every
-    checkpoint spacing K; only the grouping of the reverse sweep into single
-    and paired adjoint steps (and so the rounding of the per-cell gradient
-    sums) depends on K."""
+    """The stored states (every other step) are bitwise those of the forward
+    pass for every checkpoint spacing K; the two-step reverse pass rebuilds
+    the state between two stored ones without its Kahan term, which changes
+    it by its last rounding at most, and which states are rebuilt depends on
+    K, as does the grouping of the per-cell gradient sums.  So the gradient
+    fields agree across K to 3e-6 (measured: 1.5e-6) and the rate gradients to
+    2e-5: on this rough random state with unit adjoint sources the D gradient
+    is a sum over the grid that cancels to a small part of its terms (measured
+    spread across K: 8e-6)."""
     nx, ny, steps = 70, 50, 97
     p = small_problem(nx, ny, steps=steps)
     dU = inputs.white_noise(nx, ny, 1, -1, 1)
     dV = inputs.white_noise(nx, ny, 2, -1, 1)
     dW = inputs.white_noise(nx, ny, 3, -1, 1)
     base = gpu_adjoint(torch, p, steps, dU, dV, dW, checkpoint_every=0)
-    for K in (1, 7, 96, 97, 500):
+    for K in (1, 2, 7, 96, 97, 500):
         r = gpu_adjoint(torch, p, steps, dU, dV, dW, checkpoint_every=K)
         for k in ("theta", "lambda1", "lambda2", "u0", "v0", "w0"):
-            assert rel_err(r[k], base[k]) <= 1e-6, (K, k)
-        assert np.allclose(r["scalars"], base["scalars"], rtol=1e-6, atol=0)
+            assert rel_err(r[k], base[k]) <= 3e-6, (K, k)
+        assert np.allclose(r["scalars"], base["scalars"], rtol=2e-5, atol=0), K
 
 
 def test_workspace_reuse_and_release(torch):
