@@ -61,10 +61,14 @@ constexpr int kFlushEvery = 64;  // FP32 per-cell gradient sums are folded into 
 extern __shared__ float2 g_adj_ring[];
 
 // The two-step pass carries three levels (the rebuilt forward step and two
-// reverse steps): capped at 192 registers it keeps 10 warps per SM without
-// spills (214 registers and 9 warps uncapped).
+// reverse steps) in about 200 registers: two warps on each of the SM's four
+// schedulers (a scheduler's register file holds 16384 registers, so a third
+// warp needs 170 or fewer).  Measured, a cap of 168 registers (three warps a
+// scheduler) spilled and ran 1.8x slower, and passing the carried rows
+// through shared memory instead (166 registers, twelve warps per SM) made the
+// pass bound by shared-memory traffic and 23 % slower.
 template <int STEPS, bool KAHAN>
-__global__ void __maxnreg__(192) adjw_kernel(const adjw::PassArgs a, const Rates32 k, const int H, const int nstrips,
+__global__ void __launch_bounds__(32) adjw_kernel(const adjw::PassArgs a, const Rates32 k, const int H, const int nstrips,
                                              const int nwarps)
 {
     const int gw = blockIdx.x;

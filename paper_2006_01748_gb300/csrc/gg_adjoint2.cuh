@@ -11,11 +11,10 @@
 // that the one-step and two-step marches below give the same bits per cell.
 //
 // Rows stream through a per-warp shared-memory ring filled with cp.async,
-// two rows ahead, each lane copying and reading back only its own pair (no
-// barrier).  A ring slot holds one input row (the state X, the incoming
-// lambda with its Kahan terms, the tensor weights; in the two-step march
-// also the state of the earlier step) and the per-cell gradient sums of the
-// row written at the tick that consumes the slot.  A level reads its own and
+// one row ahead, each lane copying and reading back only its own pair (no
+// barrier).  A ring slot holds one input row (the stored state X^k, the
+// incoming lambda with its Kahan terms, the tensor weights) and the per-cell
+// gradient sums of the row written at the tick that consumes the slot.  A level reads its own and
 // north rows from the ring instead of keeping them in registers.
 #include "gg_stepw2.cuh"
 
@@ -264,6 +263,18 @@ struct RateSums2 {
         const float2 e = add2(sub2(acc[q], sub2(s, z)), sub2(x, z));
         accc[q] = sub2(accc[q], e);
         acc[q] = s;
+    }
+    // a lane outside the chunk's columns adds zeros: an exact no-op for the D
+    // sum; for the others it folds the running compensation in, which leaves
+    // the sum within its rounding.  Unlike a branch around add_all it keeps
+    // the four terms from staying live across the code that follows.
+    __device__ __forceinline__ void add_all_masked(const Out& o, bool on)
+    {
+        const float2 z = make_float2(0.0f, 0.0f);
+        add(0, on ? o.s_delta : z);
+        add(1, on ? o.s_rho : z);
+        add_two_sum(2, on ? o.s_D : z);
+        add(3, on ? o.s_c : z);
     }
     __device__ __forceinline__ void add_all(const Out& o)
     {
@@ -514,7 +525,7 @@ __device__ __forceinline__ void march(const PassArgs& a, const Rates32& kr, cons
     float2 xuP = z, xvP = z, xwP = z;
     float2 u0P = z, v0P = z, w0P = z, S2w = z;
     float2 lvP = z, lwP = z, clvP = z, clwP = z, luP = z, cluP = z;
-    float2 ax1 = z, b1 = z, ay1 = z, ax2 = z, b2 = z, ay2 = z;
+    float2 ax2 = z, b2 = z, ay2 = z;
     float2 d11c = z, d12c = z, d22c = z;
 
     // rows r0 - 2 .. r0 + kAhead - 1 in flight before the first tick
@@ -551,6 +562,7 @@ __device__ __forceinline__ void march(const PassArgs& a, const Rates32& kr, cons
             P1.lv = s2[F_LV * 32]; P1.lw = s2[F_LW * 32];
             if (KAHAN) { P1.clv = s2[F_CLV * 32]; P1.clw = s2[F_CLW * 32]; }
             else { P1.clv = P1.clw = z; }
+            const float2 ax1 = s2[F_AX * 32], b1 = s2[F_B * 32], ay1 = s2[F_AY * 32];
             P1.b = b1; P1.ay = ay1;
             N1.u = xu; N1.v = xv; N1.w = xw;
             N1.lv = s1[F_LV * 32]; N1.lw = s1[F_LW * 32];
@@ -559,6 +571,8 @@ __device__ __forceinline__ void march(const PassArgs& a, const Rates32& kr, cons
             N1.b = bF; N1.ay = ayF;
             const float2 lu1 = s2[F_LU * 32], clu1 = KAHAN ? s2[F_CLU * 32] : z;
             const Out o1 = adj_level2<KAHAN, EDGE, YEDGE>(k, S1w, P1, N1, lu1, clu1, ax1, m, q1 > 0, q1 + 1 < ny, c1);
+            // A1's rate terms count where its row is the chunk's
+            if (q1 >= ys && q1 < ye) sums.add_all_masked(o1, outc);
             // A2: row r - 3 of lambda^k (step k, state X^k)
             const int q2 = r - 3;
             Row P2, N2;
@@ -571,15 +585,12 @@ __device__ __forceinline__ void march(const PassArgs& a, const Rates32& kr, cons
             o = adj_level2<KAHAN, EDGE, YEDGE>(k, S2w, P2, N2, luP, cluP, ax2, m, q2 > 0, q2 + 1 < ny, c2);
             qw = q2;
             dc1 = d11c; dc2 = d12c; dc3 = d22c;
-            // A1's rate terms count where its row is the chunk's
-            if (q1 >= ys && q1 < ye && outc) sums.add_all(o1);
             // rows move on: F's row r - 1 becomes A1's own row, X^k row r - 2
             // and A1's lambda row r - 2 become A2's own row
             S1w = xwP; xuP = xu; xvP = xv; xwP = xw;
             S2w = w0P; u0P = N2.u; v0P = N2.v; w0P = N2.w;
             lvP = o1.lv; lwP = o1.lw; clvP = o1.clv; clwP = o1.clw; luP = o1.lu; cluP = o1.clu;
             ax2 = ax1; b2 = b1; ay2 = ay1;
-            ax1 = axF; b1 = bF; ay1 = ayF;
             d11c = o1.d11; d12c = o1.d12; d22c = o1.d22;
         }
         if (qw >= ys && qw < ye && outc) {
