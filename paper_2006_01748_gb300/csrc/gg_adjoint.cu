@@ -366,10 +366,12 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
         out3[0] = (float*)b; out3[1] = (float*)(b + fstride); out3[2] = (float*)(b + 2 * fstride);
     };
 
-    // 1. forward pass, storing the state (with Kahan terms) at the start of every
-    // segment and the states at even steps of the trailing segments
+    // 1. forward pass, storing the state at the start of every segment (with
+    // its Kahan terms where the segment is recomputed from it) and the states
+    // at even steps of the trailing segments
     for (int seg = 0; seg < nseg && e == cudaSuccess; ++seg) {
-        for (int f = 0; f < nstate && e == cudaSuccess; ++f)
+        const int nf = seg < seg_kept ? nstate : 3;
+        for (int f = 0; f < nf && e == cudaSuccess; ++f)
             e = cudaMemcpyAsync(w->ckpt[(size_t)seg * nstate + f], s->f32[s->cur][f], fbytes, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) break;
         const int64_t len = std::min<int64_t>(K, N - (int64_t)seg * K);
