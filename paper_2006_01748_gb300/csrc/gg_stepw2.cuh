@@ -263,16 +263,19 @@ __device__ __forceinline__ void warp_pass2(const Grid32& g, const Rates32& k, co
                     // intermediate level: also write the own rows of step s0 + t
                     // (a level whose destination is null writes nothing)
                     const int li = (t < T) ? t - 1 : 0;
+                    // (streaming stores: the stash is read back only by the
+                    // reverse sweep, long after the pass, so it is written
+                    // evict-first and leaves the pass's own rows in L2)
                     if (q >= ys && q < hiT && outp && stash->u[li]) {
                         const size_t o = (size_t)q * pitch + ca;
                         if (!EDGE || b_in) {
-                            *reinterpret_cast<float2*>(stash->u[li] + o) = uo;
-                            *reinterpret_cast<float2*>(stash->v[li] + o) = vo;
-                            *reinterpret_cast<float2*>(stash->w[li] + o) = wo;
+                            __stcs(reinterpret_cast<float2*>(stash->u[li] + o), uo);
+                            __stcs(reinterpret_cast<float2*>(stash->v[li] + o), vo);
+                            __stcs(reinterpret_cast<float2*>(stash->w[li] + o), wo);
                         } else {
-                            stash->u[li][o] = uo.x;
-                            stash->v[li][o] = vo.x;
-                            stash->w[li][o] = wo.x;
+                            __stcs(stash->u[li] + o, uo.x);
+                            __stcs(stash->v[li] + o, vo.x);
+                            __stcs(stash->w[li] + o, wo.x);
                         }
                     }
                 }
