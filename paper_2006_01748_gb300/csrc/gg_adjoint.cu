@@ -127,16 +127,24 @@ AdjGeom adj_geom(int steps, bool kahan, int nx, int ny)
     return kahan ? adjw_geom<2, true>(nx, ny) : adjw_geom<2, false>(nx, ny);
 }
 
-// g64 += g32; g32 = 0 (pitched, 3 fields)
-__global__ void flush_kernel(float* g1, float* g2, float* g3, double* h1, double* h2, double* h3, int nx, int ny,
-                             int pitch)
+// g64 += g32; g32 = 0 for the 3 fields, over the whole pitched area in
+// groups of 4 (the pitch is a multiple of 32 cells and the padding columns
+// hold zeros, which the reverse passes never write).
+__device__ __forceinline__ void flush4(float* g, double* h, size_t q)
 {
-    const size_t n = (size_t)ny * pitch;
-    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-        if ((int)(q % pitch) >= nx) continue;
-        h1[q] += (double)g1[q]; g1[q] = 0.0f;
-        h2[q] += (double)g2[q]; g2[q] = 0.0f;
-        h3[q] += (double)g3[q]; g3[q] = 0.0f;
+    const float4 a = reinterpret_cast<const float4*>(g)[q];
+    double2* hp = reinterpret_cast<double2*>(h) + 2 * q;
+    double2 h0 = hp[0], h1 = hp[1];
+    h0.x += (double)a.x; h0.y += (double)a.y; h1.x += (double)a.z; h1.y += (double)a.w;
+    hp[0] = h0; hp[1] = h1;
+    reinterpret_cast<float4*>(g)[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+__global__ void flush_kernel(float* g1, float* g2, float* g3, double* h1, double* h2, double* h3, size_t n4)
+{
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (size_t)gridDim.x * blockDim.x) {
+        flush4(g1, h1, q);
+        flush4(g2, h2, q);
+        flush4(g3, h3, q);
     }
 }
 
@@ -408,8 +416,9 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
     int lb = 0;          // current lam buffer
     int since_flush = 0;
     auto flush = [&]() {
-        flush_kernel<<<blocks_for((size_t)s->pitch * s->ny), 256, 0, st>>>(w->g32[0], w->g32[1], w->g32[2], w->g64[0],
-                                                                          w->g64[1], w->g64[2], s->nx, s->ny, s->pitch);
+        const size_t n4 = (size_t)s->pitch * s->ny / 4;
+        flush_kernel<<<blocks_for(n4), 256, 0, st>>>(w->g32[0], w->g32[1], w->g32[2], w->g64[0], w->g64[1], w->g64[2],
+                                                     n4);
         since_flush = 0;
         return cudaGetLastError();
     };
