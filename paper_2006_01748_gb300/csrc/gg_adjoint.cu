@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(32) adjw_kernel(const adjw::PassArgs a, const 
 {
     const int gw = blockIdx.x;
     if (gw >= nwarps) return;
+    chained_wait();  // launched with launch_chained
     const int strip = gw % nstrips, chunk = gw / nstrips;
     const int x0 = strip * adjw::Geom<STEPS>::OUT - adjw::Geom<STEPS>::HLP;
     const int ys = chunk * H;
@@ -470,19 +471,25 @@ extern "C" int gg_adjoint(gg_sim* s, int64_t nsteps, const float* dLdu_N, const 
         };
         auto single = [&](int k1) {
             const adjw::PassArgs a = pass_args(k1);
-            if (kahan) adjw_kernel<1, true><<<g1.warps, 32, adjw::kRingBytes, st>>>(a, r, g1.H, g1.strips, g1.warps);
-            else adjw_kernel<1, false><<<g1.warps, 32, adjw::kRingBytes, st>>>(a, r, g1.H, g1.strips, g1.warps);
+            const cudaError_t le =
+                kahan ? launch_chained(adjw_kernel<1, true>, g1.warps, 32, adjw::kRingBytes, st, a, r, g1.H, g1.strips,
+                                       g1.warps)
+                      : launch_chained(adjw_kernel<1, false>, g1.warps, 32, adjw::kRingBytes, st, a, r, g1.H, g1.strips,
+                                       g1.warps);
             lb ^= 1;
             since_flush += 1;
-            return cudaGetLastError();
+            return le;
         };
         auto pair = [&](int k1) {  // steps k1 and k1 - 1
             const adjw::PassArgs a = pass_args(k1 - 1);
-            if (kahan) adjw_kernel<2, true><<<g2.warps, 32, adjw::kRingBytes, st>>>(a, r, g2.H, g2.strips, g2.warps);
-            else adjw_kernel<2, false><<<g2.warps, 32, adjw::kRingBytes, st>>>(a, r, g2.H, g2.strips, g2.warps);
+            const cudaError_t le =
+                kahan ? launch_chained(adjw_kernel<2, true>, g2.warps, 32, adjw::kRingBytes, st, a, r, g2.H, g2.strips,
+                                       g2.warps)
+                      : launch_chained(adjw_kernel<2, false>, g2.warps, 32, adjw::kRingBytes, st, a, r, g2.H, g2.strips,
+                                       g2.warps);
             lb ^= 1;
             since_flush += 2;
-            return cudaGetLastError();
+            return le;
         };
         if ((len & 1) && e == cudaSuccess) {
             e = single(kr);

@@ -168,4 +168,34 @@ cudaError_t launch_adapt(const F* u, const F* v, const F* w, int nx, int ny, int
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// Programmatic dependent launch for chains of passes on one stream (the
+// adjoint's stash and reverse passes): the launch may be scheduled while the
+// previous kernel of the stream is still draining, and the kernel waits for
+// that kernel's completion and memory (griddepcontrol.wait) before its first
+// global access; right after the wait it lets the next launch be scheduled.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chained(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                                  Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+#ifdef __CUDACC__
+// the device side of launch_chained
+__device__ __forceinline__ void chained_wait()
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+#endif
+
 }  // namespace gg

@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(32, min_warps2<T>()) stepw2_stash_kernel(const
 {
     const int gw = blockIdx.x;
     if (gw >= nwarps) return;
+    chained_wait();  // launched with launch_chained
     stepw2::warp_pass2_any<T, KAHAN, true>(g, live_rates(k), H, gw % nstrips, gw / nstrips, threadIdx.x, g_ring2,
                                            &st);
 }
@@ -69,8 +70,8 @@ cudaError_t launch_ws2(const Grid32& g, const Rates32& r, int H, const Stash32& 
 {
     const int nstrips = strips2<T>(g.nx);
     const int nwarps = nstrips * ((g.ny + H - 1) / H);
-    stepw2_stash_kernel<T, KAHAN><<<nwarps, 32, stepw2::Ring<KAHAN>::bytes, s>>>(g, r, H, nstrips, nwarps, st);
-    return cudaGetLastError();
+    return launch_chained(stepw2_stash_kernel<T, KAHAN>, nwarps, 32, stepw2::Ring<KAHAN>::bytes, s, g, r, H, nstrips,
+                          nwarps, st);
 }
 
 template <int T, bool KAHAN>
