@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(32) stepw_kernel(const Grid32 g, const Rates32
     const int lane = threadIdx.x;
     const int gw = blockIdx.x;
     if (gw >= nwarps) return;
+    chained_wait();  // launched with launch_chained
     const int strip = gw % nstrips, chunk = gw / nstrips;
     stepw::warp_pass_any<T, KAHAN>(g, live_rates(k), H, strip, chunk, lane);
 }
@@ -35,6 +36,7 @@ __global__ void __launch_bounds__(128, KAHAN ? 6 : 8) stepw1_kernel(const Grid32
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (gw >= nwarps) return;  // whole warps only
+    chained_wait();            // launched with launch_chained
     const int strip = gw % nstrips, chunk = gw / nstrips;
     stepw::warp_pass_any<1, KAHAN>(g, live_rates(k), H, strip, chunk, lane);
 }
@@ -46,9 +48,10 @@ cudaError_t launch_w(const Grid32& g, const Rates32& r, int H, cudaStream_t s)
     const int nstrips = (g.nx + OUT - 1) / OUT;
     const int nchunks = (g.ny + H - 1) / H;
     const int nwarps = nstrips * nchunks;
-    if constexpr (T == 1) stepw1_kernel<KAHAN><<<(nwarps + 3) / 4, 128, 0, s>>>(g, r, H, nstrips, nwarps);
-    else stepw_kernel<T, KAHAN><<<nwarps, 32, 0, s>>>(g, r, H, nstrips, nwarps);
-    return cudaGetLastError();
+    if constexpr (T == 1)
+        return launch_chained(stepw1_kernel<KAHAN>, (nwarps + 3) / 4, 128, 0, s, g, r, H, nstrips, nwarps);
+    else
+        return launch_chained(stepw_kernel<T, KAHAN>, nwarps, 32, 0, s, g, r, H, nstrips, nwarps);
 }
 
 template <int T, bool KAHAN>

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(32, min_warps2<T>()) stepw2_kernel(const Grid3
 {
     const int gw = blockIdx.x;
     if (gw >= nwarps) return;
+    chained_wait();  // launched with launch_chained
     stepw2::warp_pass2_any<T, KAHAN>(g, live_rates(k), H, gw % nstrips, gw / nstrips, threadIdx.x, g_ring2);
 }
 
@@ -37,6 +38,7 @@ __global__ void __launch_bounds__(128) stepw2_1_kernel(const Grid32 g, const Rat
     const int wid = threadIdx.x >> 5;
     const int gw = blockIdx.x * 4 + wid;
     if (gw >= nwarps) return;  // whole warps only
+    chained_wait();            // launched with launch_chained
     stepw2::warp_pass2_any<1, KAHAN>(g, live_rates(k), H, gw % nstrips, gw / nstrips, threadIdx.x & 31,
                                      g_ring2 + wid * (stepw2::Ring<KAHAN>::bytes / 8));
 }
@@ -60,9 +62,10 @@ cudaError_t launch_w2(const Grid32& g, const Rates32& r, int H, cudaStream_t s)
     const int nstrips = strips2<T>(g.nx);
     const int nwarps = nstrips * ((g.ny + H - 1) / H);
     constexpr int rb = stepw2::Ring<KAHAN>::bytes;
-    if constexpr (T == 1) stepw2_1_kernel<KAHAN><<<(nwarps + 3) / 4, 128, 4 * rb, s>>>(g, r, H, nstrips, nwarps);
-    else stepw2_kernel<T, KAHAN><<<nwarps, 32, rb, s>>>(g, r, H, nstrips, nwarps);
-    return cudaGetLastError();
+    if constexpr (T == 1)
+        return launch_chained(stepw2_1_kernel<KAHAN>, (nwarps + 3) / 4, 128, 4 * rb, s, g, r, H, nstrips, nwarps);
+    else
+        return launch_chained(stepw2_kernel<T, KAHAN>, nwarps, 32, rb, s, g, r, H, nstrips, nwarps);
 }
 
 template <int T, bool KAHAN>
