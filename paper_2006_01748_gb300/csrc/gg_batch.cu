@@ -673,7 +673,9 @@ int gg_batch_autotune(gg_batch* b, int64_t trial_steps, int32_t* chosen)
     std::vector<Plan32> cands;
     for (int mode : {kModePersistent, kModePasses, kModePasses2})
         for (int T = 1; T <= kBatchMaxT; ++T) {
-            const std::vector<int> bys = {32, 64, 128, 256};
+            // intermediate heights: on the 256-instance workload 40-56-row chunks
+            // ran 4 % faster than 32 or 64 (halo rows against whole waves)
+            const std::vector<int> bys = {32, 40, 48, 56, 64, 96, 128, 256};
             for (int by : bys) {
                 if (by < 4 * T + 8) continue;
                 Plan32 p;
@@ -708,25 +710,41 @@ int gg_batch_autotune(gg_batch* b, int64_t trial_steps, int32_t* chosen)
     cudaEventCreate(&e1);
     const Plan32 orig = b->plan;
     const int orig_cur = b->cur;
-    double best = 1e300;
     Plan32 bestp = orig;
     int rc = GG_OK;
-    for (const Plan32& p : cands) {
-        if (e != cudaSuccess) break;
+    // per-step device time of plan p over about `steps` steps, the least of
+    // `reps` timed runs after one untimed run
+    auto time_plan = [&](const Plan32& p, int64_t steps, int reps) -> double {
+        double t = 1e300;
         rc = configure(b, p);
-        if (rc != GG_OK) break;
-        const int64_t n = std::max<int64_t>(trial_steps / p.T, 1) * p.T;
+        if (rc != GG_OK) return t;
+        const int64_t n = std::max<int64_t>(steps / p.T, 1) * p.T;
         rc = enqueue_steps(b, n, b->cur, b->stream);  // warm-up
-        if (rc != GG_OK) break;
-        cudaEventRecord(e0, b->stream);
-        rc = enqueue_steps(b, n, b->cur, b->stream);
-        cudaEventRecord(e1, b->stream);
-        if (rc != GG_OK) break;
-        e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const double per_step = ms / (double)n;
-        if (per_step < best) { best = per_step; bestp = p; }
+        for (int rep = 0; rep < reps && rc == GG_OK && e == cudaSuccess; ++rep) {
+            cudaEventRecord(e0, b->stream);
+            rc = enqueue_steps(b, n, b->cur, b->stream);
+            cudaEventRecord(e1, b->stream);
+            if (rc != GG_OK) break;
+            e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t = std::min(t, ms / (double)n);
+        }
+        return t;
+    };
+    // a short trial of every candidate, then the three fastest again over
+    // four times as many steps, best of two
+    std::vector<std::pair<double, size_t>> trial;
+    for (size_t i = 0; i < cands.size() && rc == GG_OK && e == cudaSuccess; ++i)
+        trial.push_back({time_plan(cands[i], trial_steps, 1), i});
+    std::sort(trial.begin(), trial.end());
+    double best = 1e300;
+    for (size_t j = 0; j < trial.size() && j < 3 && rc == GG_OK && e == cudaSuccess; ++j) {
+        const double t = time_plan(cands[trial[j].second], 4 * trial_steps, 2);
+        if (rc == GG_OK && e == cudaSuccess && t < best) {
+            best = t;
+            bestp = cands[trial[j].second];
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
