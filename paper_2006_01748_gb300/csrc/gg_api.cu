@@ -451,7 +451,8 @@ int gg_create(const gg_grid* grid, const gg_params* params, const double* theta,
     // Stage the six host arrays on the device (dense FP64), then build the
     // tensor and the pitched state.
     double* staging = nullptr;
-    const size_t nstage = fp64 ? 6 : 3;  // FP32 keeps theta/l1/l2 in the arena
+    // FP32 keeps theta/l1/l2 in the arena and stages a11 / a22 for the face weights
+    const size_t nstage = fp64 ? 6 : 5;
     e = cudaMalloc(&staging, dense_stride * nstage);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -472,7 +473,8 @@ int gg_create(const gg_grid* grid, const gg_params* params, const double* theta,
     if (e == cudaSuccess)
         e = launch_coefficients(dth, dl1, dl2, s->nx, s->ny, s->dx, s->dy, fp64 ? (void*)s->a64[0] : (void*)s->a32[0],
                                 fp64 ? (void*)s->a64[1] : (void*)s->a32[1], fp64 ? (void*)s->a64[2] : (void*)s->a32[2],
-                                s->pitch, fp64, s->counters, s->counters + 2, s->stream);
+                                s->pitch, fp64, fp64 ? nullptr : (double*)((char*)staging + 3 * dense_stride),
+                                s->counters, s->counters + 2, s->stream);
     const double* dstate[3] = {du0, dv0, dw0};
     for (int f = 0; f < 3 && e == cudaSuccess; ++f)
         e = launch_unpack(dstate[f], true, fp64 ? (void*)s->f64[0][f] : (void*)s->f32[0][f], fp64, s->nx, s->ny,

@@ -107,13 +107,14 @@ cudaError_t launch_step64(const Grid64& g, const Rates64& r, cudaStream_t s);
 
 // Coefficients of eq. (2) and validation counters.  fp64: a11, a12, a22
 // per cell (pitched doubles) into c0, c1, c2; otherwise the FP32 coefficient
-// fields ax, b, ay of Grid32 into c0, c1, c2 (dx, dy used only then).
+// fields ax, b, ay of Grid32 into c0, c1, c2 (dx, dy and scratch, two dense
+// FP64 arrays of nx * ny, used only then).
 // counters[0]: cells with lambda <= 0 or non-finite theta/lambda;
 // counters[1]: non-finite initial values; lmax_bits: max lambda_max as the
 // bit pattern of a non-negative double (atomicMax on unsigned long long).
 cudaError_t launch_coefficients(const double* theta, const double* l1, const double* l2, int nx, int ny,
                                 double dx, double dy, void* c0, void* c1, void* c2, int pitch, bool fp64,
-                                unsigned long long* counters, unsigned long long* lmax_bits,
+                                double* scratch, unsigned long long* counters, unsigned long long* lmax_bits,
                                 cudaStream_t s);
 // One entry of eq. (2) (which = 0: a11, 1: a12, 2: a22) per cell from dense
 // FP64 theta / lambda, into a dense buffer of n floats or doubles.

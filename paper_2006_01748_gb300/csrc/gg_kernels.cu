@@ -83,11 +83,12 @@ __device__ __forceinline__ void tensor_at(double th, double L1, double L2, doubl
 // FP64 kernels get a11, a12, a22 per cell.  FP32 kernels get the face
 // weights ax = (a11 + a11_east) kx, ay = (a22 + a22_north) ky (0 on the last
 // column / row, whose east / north face is a boundary face) and b = a12 kc,
-// computed in FP64 and rounded once.
+// computed in FP64 and rounded once: this kernel writes b and the cell's a11
+// and a22 (dense FP64, t11 / t22), faces_kernel the two face weights.
 template <bool FACES, typename F>
 __global__ void coefficients_kernel(const double* __restrict__ theta, const double* __restrict__ l1,
-                                    const double* __restrict__ l2, int nx, int ny, double kx, double ky, double kc,
-                                    F* c0, F* c1, F* c2, int pitch, unsigned long long* counters,
+                                    const double* __restrict__ l2, int nx, int ny, double kc, F* c0, F* c1,
+                                    F* c2, double* t11, double* t22, int pitch, unsigned long long* counters,
                                     unsigned long long* lmax_bits)
 {
     __shared__ double smax[32];
@@ -103,12 +104,9 @@ __global__ void coefficients_kernel(const double* __restrict__ theta, const doub
         tensor_at(th, L1, L2, A11, A12, A22);
         const size_t o = (size_t)j * pitch + i;
         if constexpr (FACES) {
-            double e11 = 0.0, e12 = 0.0, e22 = 0.0, n11 = 0.0, n12 = 0.0, n22 = 0.0;
-            if (i + 1 < nx) tensor_at(theta[q + 1], l1[q + 1], l2[q + 1], e11, e12, e22);
-            if (j + 1 < ny) tensor_at(theta[q + nx], l1[q + nx], l2[q + nx], n11, n12, n22);
-            c0[o] = (F)(i + 1 < nx ? (A11 + e11) * kx : 0.0);
+            t11[q] = A11;
+            t22[q] = A22;
             c1[o] = (F)(A12 * kc);
-            c2[o] = (F)(j + 1 < ny ? (A22 + n22) * ky : 0.0);
         } else {
             c0[o] = (F)A11;
             c1[o] = (F)A12;
@@ -137,6 +135,20 @@ __global__ void coefficients_kernel(const double* __restrict__ theta, const doub
         }
         if (b) atomicAdd(&counters[0], b);
         atomicMax(lmax_bits, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// ax and ay of the FP32 kernels from the dense a11 / a22 of coefficients_kernel.
+template <typename F>
+__global__ void faces_kernel(const double* __restrict__ t11, const double* __restrict__ t22, int nx, int ny,
+                             double kx, double ky, F* c0, F* c2, int pitch)
+{
+    const size_t n = (size_t)nx * ny;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(q / nx), i = (int)(q % nx);
+        const size_t o = (size_t)j * pitch + i;
+        c0[o] = (F)(i + 1 < nx ? (t11[q] + t11[q + 1]) * kx : 0.0);
+        c2[o] = (F)(j + 1 < ny ? (t22[q] + t22[q + nx]) * ky : 0.0);
     }
 }
 
@@ -311,19 +323,27 @@ cudaError_t launch_step64(const Grid64& g, const Rates64& r, cudaStream_t s)
 }
 
 cudaError_t launch_coefficients(const double* theta, const double* l1, const double* l2, int nx, int ny, double dx,
-                                double dy, void* c0, void* c1, void* c2, int pitch, bool fp64,
+                                double dy, void* c0, void* c1, void* c2, int pitch, bool fp64, double* scratch,
                                 unsigned long long* counters, unsigned long long* lmax_bits, cudaStream_t s)
 {
     const size_t n = (size_t)nx * ny;
     const int blocks = blocks_for(n, 256);
-    if (fp64)
-        coefficients_kernel<false, double><<<blocks, 256, 0, s>>>(theta, l1, l2, nx, ny, 0.0, 0.0, 0.0, (double*)c0,
-                                                                  (double*)c1, (double*)c2, pitch, counters,
-                                                                  lmax_bits);
-    else
-        coefficients_kernel<true, float><<<blocks, 256, 0, s>>>(theta, l1, l2, nx, ny, 0.5 / (dx * dx),
-                                                                0.5 / (dy * dy), 0.25 / (dx * dy), (float*)c0,
-                                                                (float*)c1, (float*)c2, pitch, counters, lmax_bits);
+    if (fp64) {
+        coefficients_kernel<false, double><<<blocks, 256, 0, s>>>(theta, l1, l2, nx, ny, 0.0, (double*)c0,
+                                                                  (double*)c1, (double*)c2, nullptr, nullptr, pitch,
+                                                                  counters, lmax_bits);
+        return cudaGetLastError();
+    }
+    if (!scratch) return cudaErrorInvalidValue;
+    double* t11 = scratch;
+    double* t22 = scratch + n;
+    coefficients_kernel<true, float><<<blocks, 256, 0, s>>>(theta, l1, l2, nx, ny, 0.25 / (dx * dy), (float*)c0,
+                                                            (float*)c1, (float*)c2, t11, t22, pitch, counters,
+                                                            lmax_bits);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    faces_kernel<float><<<blocks, 256, 0, s>>>(t11, t22, nx, ny, 0.5 / (dx * dx), 0.5 / (dy * dy), (float*)c0,
+                                               (float*)c2, pitch);
     return cudaGetLastError();
 }
 
