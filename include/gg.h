@@ -224,8 +224,9 @@ int gg_front_speed(gg_sim* sim, int32_t i0, int32_t j0, int64_t nsteps, double v
  *   g_u0, g_v0, g_w0: device, nx*ny floats: dL/d(U,V,W) at step 0; may be NULL.
  *   g_scalars: host, 4 doubles: dL/d(delta, rho, D, c); may be NULL.
  *   checkpoint_every: steps between checkpoints (0 = about sqrt(nsteps)).
- * The forward pass stores a checkpoint (state and Kahan terms) at the start
- * of every segment of checkpoint_every steps; within a segment only the
+ * The forward pass stores a checkpoint (the state, with its Kahan terms
+ * where the segment is recomputed later) at the start of every segment of
+ * checkpoint_every steps; within a segment only the
  * states at even steps are stored, and the reverse pass over a pair of steps
  * rebuilds the state between two stored ones from the earlier (without its
  * Kahan term: it differs from the forward's by its last rounding at most).
