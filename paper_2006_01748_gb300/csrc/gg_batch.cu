@@ -153,8 +153,11 @@ __global__ void __launch_bounds__(32) pass_kernel(const InstDesc* __restrict__ d
 // shared-memory ring as dynamic shared memory).
 extern __shared__ float2 g_batch_ring[];
 
+// T = 3 and 4 are bound to 12 warps per SM (168 registers: three warps per
+// scheduler); the T = 3 Kahan pass otherwise takes 170 registers and runs
+// two warps per scheduler.
 template <int T, bool KAHAN>
-__global__ void __launch_bounds__(32, T == 4 ? 12 : 1) pass2_kernel(const InstDesc* __restrict__ desc,
+__global__ void __launch_bounds__(32, T >= 3 ? 12 : 1) pass2_kernel(const InstDesc* __restrict__ desc,
                                                                     const int2* __restrict__ items, int nitems,
                                                                     int parity, int variant, int H)
 {
