@@ -194,7 +194,7 @@ Plan32 tune_plan(gg_sim* s, int64_t trial_steps)
         if (wave > 0 && strips <= wave) {
             int added = 0;
             for (int m = 1; added < 4; ++m) {
-                const int nch = m * (wave / strips);
+                const int nch = (int)((int64_t)m * wave / strips);  // chunk rows filling m waves
                 const int H = (s->ny + nch - 1) / nch;
                 if (H < 4 * T + 8) break;
                 if (H > 256) continue;
@@ -217,7 +217,7 @@ Plan32 tune_plan(gg_sim* s, int64_t trial_steps)
         if (wave2 > 0 && strips2 <= wave2) {
             int added = 0;
             for (int m = 1; added < 4; ++m) {
-                const int nch = m * (wave2 / strips2);
+                const int nch = (int)((int64_t)m * wave2 / strips2);  // chunk rows filling m waves
                 const int H = (s->ny + nch - 1) / nch;
                 if (H < 4 * T + 8) break;
                 if (H > 256) continue;
