@@ -9,9 +9,9 @@
         3 passes of each warp plan, one and two columns per lane (T = 1..4,
         chunks 64/128/256, Kahan) and of the plain FP32 T = 1 plans, one line
         per plan on stdout
-    python -m paper_2006_01748_gb300.prof adjoint --nx 2048 --steps 20 --kind warp2 --T 3 --chunk 42
+    python -m paper_2006_01748_gb300.prof adjoint --nx 2048 --steps 20 --kind warp2 --T 4 --chunk 42
         one gg_adjoint call on the adjoint workload (forward plan fixed, no tuning)
-    python -m paper_2006_01748_gb300.prof batch --scale 1 --steps 6 [--mode passes --T 4 --chunk 128]
+    python -m paper_2006_01748_gb300.prof batch --scale 1 --steps 6 [--mode passes2 --T 3 --chunk 56]
         the 256-instance ensemble, tuned (or with the given plan), a few steps
 
 Each run synchronises and prints what it ran; nothing is timed here (time
@@ -109,7 +109,7 @@ def main(argv=None):
     s.add_argument("--nx", type=int, default=2048)
     s.add_argument("--steps", type=int, default=20)
     s.add_argument("--kind", default="warp2", choices=["warp", "warp2"])
-    s.add_argument("--T", type=int, default=3)
+    s.add_argument("--T", type=int, default=4)
     s.add_argument("--chunk", type=int, default=42)
     s.set_defaults(fn=_adjoint)
     s = sub.add_parser("batch")
