@@ -43,15 +43,16 @@ __global__ void __launch_bounds__(128) stepw2_1_kernel(const Grid32 g, const Rat
                                      g_ring2 + wid * (stepw2::Ring<KAHAN>::bytes / 8));
 }
 
-template <int T, bool KAHAN>
+// SMASK: the levels that write the stash (bit t - 1 for level t).
+template <int T, bool KAHAN, int SMASK>
 __global__ void __launch_bounds__(32, min_warps2<T>()) stepw2_stash_kernel(const Grid32 g, const Rates32 k, const int H,
                                                           const int nstrips, const int nwarps, const Stash32 st)
 {
     const int gw = blockIdx.x;
     if (gw >= nwarps) return;
     chained_wait();  // launched with launch_chained
-    stepw2::warp_pass2_any<T, KAHAN, true>(g, live_rates(k), H, gw % nstrips, gw / nstrips, threadIdx.x, g_ring2,
-                                           &st);
+    stepw2::warp_pass2_any<T, KAHAN, SMASK>(g, live_rates(k), H, gw % nstrips, gw / nstrips, threadIdx.x, g_ring2,
+                                            &st);
 }
 
 template <int T> inline int strips2(int nx) { return (nx + stepw2::Geom<T>::OUT - 1) / stepw2::Geom<T>::OUT; }
@@ -68,13 +69,38 @@ cudaError_t launch_w2(const Grid32& g, const Rates32& r, int H, cudaStream_t s)
         return launch_chained(stepw2_kernel<T, KAHAN>, nwarps, 32, rb, s, g, r, H, nstrips, nwarps);
 }
 
-template <int T, bool KAHAN>
-cudaError_t launch_ws2(const Grid32& g, const Rates32& r, int H, const Stash32& st, cudaStream_t s)
+template <int T, bool KAHAN, int SMASK>
+cudaError_t launch_ws2m(const Grid32& g, const Rates32& r, int H, const Stash32& st, cudaStream_t s)
 {
     const int nstrips = strips2<T>(g.nx);
     const int nwarps = nstrips * ((g.ny + H - 1) / H);
-    return launch_chained(stepw2_stash_kernel<T, KAHAN>, nwarps, 32, stepw2::Ring<KAHAN>::bytes, s, g, r, H, nstrips,
-                          nwarps, st);
+    return launch_chained(stepw2_stash_kernel<T, KAHAN, SMASK>, nwarps, 32, stepw2::Ring<KAHAN>::bytes, s, g, r, H,
+                          nstrips, nwarps, st);
+}
+
+// The stash set of a pass is that of its destinations (the non-null ones).
+// The adjoint stores the states at even steps, so level t of a pass from step
+// s0 writes when s0 + t is even: for T = 4 levels {2} (s0 even) or {1, 3}
+// (s0 odd), for T = 3 {2} or {1}, for T = 2 none or {1}.  Those sets have
+// kernels; a pass that writes no level runs the plain kernel, any other set is
+// refused.
+template <int T, bool KAHAN>
+cudaError_t launch_ws2(const Grid32& g, const Rates32& r, int H, const Stash32& st, cudaStream_t s)
+{
+    int m = 0;
+    for (int li = 0; li < T - 1; ++li)
+        if (st.u[li]) m |= 1 << li;
+    if (m == 0) return launch_w2<T, KAHAN>(g, r, H, s);
+    if constexpr (T == 2) {
+        if (m == 1) return launch_ws2m<2, KAHAN, 1>(g, r, H, st, s);
+    } else if constexpr (T == 3) {
+        if (m == 2) return launch_ws2m<3, KAHAN, 2>(g, r, H, st, s);
+        if (m == 1) return launch_ws2m<3, KAHAN, 1>(g, r, H, st, s);
+    } else {
+        if (m == 2) return launch_ws2m<4, KAHAN, 2>(g, r, H, st, s);
+        if (m == 5) return launch_ws2m<4, KAHAN, 5>(g, r, H, st, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int T, bool KAHAN>

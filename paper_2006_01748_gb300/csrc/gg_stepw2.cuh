@@ -75,13 +75,13 @@ template <int N> __device__ __forceinline__ void cp_async_wait()
 
 // EDGE: the strip touches the west or east domain boundary.  YEDGE: the
 // chunk's rows (with their halo of T rows) touch the south or north
-// boundary.  STASH: levels 1..T-1 also write u, v, w of their own rows (those
-// with a non-null destination).
+// boundary.  SMASK: level t (1 <= t < T) with bit t - 1 set also writes u, v,
+// w of its own rows to the stash (a compile-time set: no test per tick).
 // ring: this warp's Ring<KAHAN>::bytes of shared memory.  The ring is read
 // with ordinary shared-memory loads, which the compiler keeps in program order
 // with the cp.async copies (their asm statements clobber memory); a slot is
 // refilled only after the loads of the row it held were issued.
-template <int T, bool KAHAN, bool EDGE, bool STASH = false, bool YEDGE = true>
+template <int T, bool KAHAN, bool EDGE, int SMASK = 0, bool YEDGE = true>
 __device__ __forceinline__ void warp_pass2(const Grid32& g, const Rates32& k, const int H, const int strip,
                                            const int chunk, const int lane, float2* ring,
                                            const Stash32* stash = nullptr)
@@ -259,14 +259,14 @@ __device__ __forceinline__ void warp_pass2(const Grid32& g, const Rates32& k, co
                     }
                 }
             } else {
-                if constexpr (STASH) {
-                    // intermediate level: also write the own rows of step s0 + t
-                    // (a level whose destination is null writes nothing)
+                if constexpr (SMASK != 0) {
+                    // intermediate level in the stash set: also write the own
+                    // rows of step s0 + t (streaming stores: the stash is read
+                    // back only by the reverse sweep, long after the pass, so
+                    // it is written evict-first and leaves the pass's own rows
+                    // in L2)
                     const int li = (t < T) ? t - 1 : 0;
-                    // (streaming stores: the stash is read back only by the
-                    // reverse sweep, long after the pass, so it is written
-                    // evict-first and leaves the pass's own rows in L2)
-                    if (q >= ys && q < hiT && outp && stash->u[li]) {
+                    if (((SMASK >> li) & 1) && q >= ys && q < hiT && outp) {
                         const size_t o = (size_t)q * pitch + ca;
                         if (!EDGE || b_in) {
                             __stcs(reinterpret_cast<float2*>(stash->u[li] + o), uo);
@@ -300,7 +300,7 @@ __device__ __forceinline__ void warp_pass2(const Grid32& g, const Rates32& k, co
 }
 
 // Runs warp_pass2 with the variant that matches the warp's position.
-template <int T, bool KAHAN, bool STASH = false>
+template <int T, bool KAHAN, int SMASK = 0>
 __device__ __forceinline__ void warp_pass2_any(const Grid32& g, const Rates32& k, const int H, const int strip,
                                                const int chunk, const int lane, float2* ring,
                                                const Stash32* stash = nullptr)
@@ -311,10 +311,10 @@ __device__ __forceinline__ void warp_pass2_any(const Grid32& g, const Rates32& k
     const int ys = chunk * H;
     const bool yin = ys - T >= 1 && ys + H + T <= g.ny - 1;
     if (xin) {
-        if (yin) warp_pass2<T, KAHAN, false, STASH, false>(g, k, H, strip, chunk, lane, ring, stash);
-        else warp_pass2<T, KAHAN, false, STASH, true>(g, k, H, strip, chunk, lane, ring, stash);
+        if (yin) warp_pass2<T, KAHAN, false, SMASK, false>(g, k, H, strip, chunk, lane, ring, stash);
+        else warp_pass2<T, KAHAN, false, SMASK, true>(g, k, H, strip, chunk, lane, ring, stash);
     } else {
-        warp_pass2<T, KAHAN, true, STASH, true>(g, k, H, strip, chunk, lane, ring, stash);
+        warp_pass2<T, KAHAN, true, SMASK, true>(g, k, H, strip, chunk, lane, ring, stash);
     }
 }
 

@@ -130,6 +130,35 @@ def test_checkpoint_spacing_does_not_change_the_result(torch):
         assert np.allclose(r["scalars"], base["scalars"], rtol=2e-5, atol=0), K
 
 
+@pytest.mark.parametrize("K", [0, 7])
+def test_forward_plan_does_not_change_the_adjoint(torch, K):
+    """The adjoint's forward and recompute passes run the simulation's plan
+    (its kernel kind, steps per pass and chunk height), writing the even
+    states from the intermediate levels of each pass: with T = 4 level 2
+    (passes from even steps) or levels 1 and 3 (odd), with T = 3 level 2 or
+    level 1, with T = 2 level 1 from odd steps.  Every plan gives the forward's
+    bits, so the stored states and the whole adjoint are bitwise the same
+    for every plan; 41 steps and K = 7 give passes from odd steps."""
+    nx, ny, steps = 130, 77, 41
+    p = small_problem(nx, ny, steps=steps)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda().view(-1)
+    dU = t(inputs.white_noise(nx, ny, 11, -1, 1))
+    dV = t(inputs.white_noise(nx, ny, 12, -1, 1))
+    dW = t(inputs.white_noise(nx, ny, 13, -1, 1))
+    base = None
+    for kind, T in [("warp", 1), ("warp2", 2), ("warp2", 3), ("warp2", 4), ("warp", 3), ("warp", 4)]:
+        with gg.GGSim.from_problem(p, precision="fp32_kahan") as sim:
+            sim.set_plan(kind, T, chunk=24)
+            r = sim.adjoint(steps, dU, dV, dW, checkpoint_every=K)
+            r = {k: (v.cpu().numpy() if k != "scalars" else np.asarray(v)) for k, v in r.items()}
+            r["state"] = np.stack(sim.state(fp64=False))
+        if base is None:
+            base = r
+            continue
+        for k in base:
+            assert np.array_equal(r[k], base[k]), (kind, T, k)
+
+
 def test_workspace_reuse_and_release(torch):
     """A second call on the same simulation reuses the workspace (kept
     states included) and a call after gg_adjoint_release allocates it again;
